@@ -1,0 +1,366 @@
+// Graph ingest and adjacency build (temporal graph T and its static graph G,
+// Section 2).  Everything after the input copy runs on the device: validation,
+// normalisation t' = t - t_min (Algorithm 1 assumes times start at 0), three
+// stable radix sorts that leave every adjacency segment in time order, and
+// segment offsets found from the sorted keys.
+#include <algorithm>
+#include <cstring>
+
+#include "tm_internal.cuh"
+
+namespace tmo {
+namespace {
+
+constexpr int kThreads = 256;
+
+unsigned grid_for(int64_t n, int per_sm = 8) {
+    int64_t g = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)sm_count() * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+// flags[0]: unsorted, flags[1]: id out of range (n_nodes given) or negative,
+// flags[2]: max node id
+__global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                           const int64_t* __restrict__ t, int64_t m, int32_t n_nodes,
+                           int32_t* __restrict__ flags) {
+    int32_t mx = -1;
+    int bad_sort = 0, bad_id = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = src[i], d = dst[i];
+        if (s < 0 || d < 0 || (n_nodes >= 0 && (s >= n_nodes || d >= n_nodes))) bad_id = 1;
+        mx = max(mx, max(s, d));
+        if (i > 0 && t[i] < t[i - 1]) bad_sort = 1;
+    }
+    if (__any_sync(kFull, bad_sort) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1);
+    if (__any_sync(kFull, bad_id) && (threadIdx.x & 31) == 0) atomicOr(&flags[1], 1);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&flags[2], mx);
+}
+
+__global__ void k_ingest(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                         const int64_t* __restrict__ t, int64_t m, int64_t tmin,
+                         int32_t* __restrict__ gs, int32_t* __restrict__ gd, int64_t* __restrict__ gt,
+                         uint32_t* __restrict__ key_src, uint32_t* __restrict__ key_dst,
+                         uint32_t* __restrict__ iota_a, uint32_t* __restrict__ iota_b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = src[i], d = dst[i];
+        gs[i] = s;
+        gd[i] = d;
+        gt[i] = t[i] - tmin;
+        key_src[i] = (uint32_t)s;
+        key_dst[i] = (uint32_t)d;
+        iota_a[i] = (uint32_t)i;
+        iota_b[i] = (uint32_t)i;
+    }
+}
+
+// off[v] = first position whose sorted key is >= v, for v in [0, n]
+__global__ void k_offsets(const uint32_t* __restrict__ keys, int64_t m, int32_t n,
+                          int64_t* __restrict__ off) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t prev = i == 0 ? -1 : (int64_t)keys[i - 1];
+        int64_t cur = i == m ? (int64_t)n : (int64_t)keys[i];
+        for (int64_t v = prev + 1; v <= cur; v++) off[v] = i;
+    }
+}
+
+// out_nbr/out_t (or in_*) gathered through the sort permutation
+__global__ void k_gather_view(const uint32_t* __restrict__ perm, const int32_t* __restrict__ other,
+                              const int64_t* __restrict__ t, int64_t m, int32_t* __restrict__ nbr,
+                              int64_t* __restrict__ tv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = perm[i];
+        nbr[i] = other[e];
+        tv[i] = t[e];
+    }
+}
+
+// pair view: positions sorted by (src, dst, time); head flag where the pair changes
+__global__ void k_pair_heads(const uint32_t* __restrict__ perm, const int32_t* __restrict__ src,
+                             const int32_t* __restrict__ dst, const int64_t* __restrict__ t,
+                             int64_t m, int64_t* __restrict__ head, int64_t* __restrict__ pair_t) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = perm[i];
+        pair_t[i] = t[e];
+        int64_t h = 1;
+        if (i > 0) {
+            uint32_t f = perm[i - 1];
+            h = (src[e] != src[f] || dst[e] != dst[f]) ? 1 : 0;
+        }
+        head[i] = h;
+    }
+}
+
+// pid_excl[i] = number of heads before i; a head at i starts pair pid_excl[i]
+__global__ void k_pair_index(const uint32_t* __restrict__ perm, const int32_t* __restrict__ dst,
+                             const int64_t* __restrict__ head, const int64_t* __restrict__ pid_excl,
+                             int64_t m, int32_t* __restrict__ pair_dst, int64_t* __restrict__ pair_off) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (head[i]) {
+            int64_t p = pid_excl[i];
+            pair_dst[p] = dst[perm[i]];
+            pair_off[p] = i;
+        }
+    }
+}
+
+__global__ void k_pair_tail(int64_t* __restrict__ pair_off, const int64_t* __restrict__ P, int64_t m) {
+    pair_off[*P] = m;
+}
+
+// pk_off[u] = pair index of the first pair whose source is >= u
+__global__ void k_pk_off(const int64_t* __restrict__ out_off, const int64_t* __restrict__ head,
+                         const int64_t* __restrict__ pid_excl, const int64_t* __restrict__ P,
+                         int64_t m, int32_t n, int64_t* __restrict__ pk_off) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u <= n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t pos = out_off[u];
+        pk_off[u] = pos >= m ? *P : pid_excl[pos];
+    }
+}
+
+int bits_for(int32_t n) {
+    int b = 0;
+    while (b < 31 && ((int64_t)1 << b) < (int64_t)n) b++;
+    return b;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, int64_t m,
+                int32_t n_nodes, cudaStream_t st, tm_graph** out) {
+    if (!out) { set_error("out is NULL"); return TM_EINVAL; }
+    *out = nullptr;
+    if (m < 0 || m >= ((int64_t)1 << 31) - 1) { set_error("m outside [0, 2^31-1)"); return TM_EINVAL; }
+    if (m > 0 && (!d_src || !d_dst || !d_t)) { set_error("NULL edge array"); return TM_EINVAL; }
+    if (n_nodes < -1) { set_error("n_nodes < -1"); return TM_EINVAL; }
+
+    int dev = 0;
+    TM_CUDA(cudaGetDevice(&dev));
+    PhaseEvents pe(profiling());
+    int ev0 = pe.mark(st);
+    int64_t tmin = 0, tmax = 0;
+    int32_t n = n_nodes < 0 ? 0 : n_nodes;
+    if (m > 0) {
+        int32_t* flags = nullptr;
+        TM_CUDA(cudaMallocAsync((void**)&flags, 4 * sizeof(int32_t), st));
+        int32_t init[4] = {0, 0, -1, 0};
+        TM_CUDA(cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        k_validate<<<grid_for(m), kThreads, 0, st>>>(d_src, d_dst, d_t, m, n_nodes, flags); count_launch();
+        TM_CUDA(cudaGetLastError());
+        int32_t hf[4];
+        int64_t tt[2];
+        TM_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+        TM_CUDA(cudaMemcpyAsync(&tt[0], d_t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        TM_CUDA(cudaMemcpyAsync(&tt[1], d_t + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        TM_CUDA(cudaStreamSynchronize(st));
+        cudaFreeAsync(flags, st);
+        if (hf[0]) { set_error("timestamps are not sorted non-decreasingly"); return TM_EUNSORTED; }
+        if (hf[1]) { set_error("node id outside [0, n_nodes)"); return TM_ERANGE; }
+        tmin = tt[0];
+        tmax = tt[1] - tt[0];
+        if (tt[1] < tt[0] || tmax >= ((int64_t)1 << 61)) { set_error("time span >= 2^61"); return TM_EINVAL; }
+        if (n_nodes < 0) n = hf[2] + 1;
+    }
+
+    // ---- one allocation for the resident graph
+    size_t nN = (size_t)n + 1, M = (size_t)m;
+    size_t sz_i32m = align256(4 * M), sz_i64m = align256(8 * M), sz_off = align256(8 * nN);
+    size_t total = 2 * sz_i32m + sz_i64m        // src, dst, t
+                 + sz_off + sz_i32m + sz_i64m   // out view
+                 + sz_off + sz_i32m + sz_i64m   // in view
+                 + sz_off + sz_i32m + align256(8 * (M + 1)) + sz_i64m;  // pair view (P <= m)
+    tm_graph* g = new (std::nothrow) tm_graph();
+    if (!g) { set_error("host allocation failed"); return TM_ENOMEM; }
+    g->device = dev;
+    g->m = m;
+    g->n = n;
+    g->t_min = tmin;
+    g->t_max = tmax;
+    g->bytes = (int64_t)total;
+    cudaError_t e = cudaMalloc(&g->block, total);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_status(e, "cudaMalloc(graph)", __FILE__, __LINE__);
+    }
+    char* p = (char*)g->block;
+    auto take = [&](size_t bytes) { char* r = p; p += bytes; return (void*)r; };
+    int32_t* gs = (int32_t*)take(sz_i32m);
+    int32_t* gd = (int32_t*)take(sz_i32m);
+    int64_t* gt = (int64_t*)take(sz_i64m);
+    int64_t* out_off = (int64_t*)take(sz_off);
+    int32_t* out_nbr = (int32_t*)take(sz_i32m);
+    int64_t* out_t = (int64_t*)take(sz_i64m);
+    int64_t* in_off = (int64_t*)take(sz_off);
+    int32_t* in_nbr = (int32_t*)take(sz_i32m);
+    int64_t* in_t = (int64_t*)take(sz_i64m);
+    int64_t* pk_off = (int64_t*)take(sz_off);
+    int32_t* pair_dst = (int32_t*)take(sz_i32m);
+    int64_t* pair_off = (int64_t*)take(align256(8 * (M + 1)));
+    int64_t* pair_t = (int64_t*)take(sz_i64m);
+
+    GraphDev& G = g->dev;
+    G.m = m; G.n = n;
+    G.src = gs; G.dst = gd; G.t = gt;
+    G.out_off = out_off; G.out_nbr = out_nbr; G.out_t = out_t;
+    G.in_off = in_off; G.in_nbr = in_nbr; G.in_t = in_t;
+    G.pk_off = pk_off; G.pair_dst = pair_dst; G.pair_off = pair_off; G.pair_t = pair_t;
+
+    int rc = TM_OK;
+    if (m == 0) {
+        TM_CUDA(cudaMemsetAsync(out_off, 0, 8 * nN, st));
+        TM_CUDA(cudaMemsetAsync(in_off, 0, 8 * nN, st));
+        TM_CUDA(cudaMemsetAsync(pk_off, 0, 8 * nN, st));
+        TM_CUDA(cudaMemsetAsync(pair_off, 0, 8, st));
+        TM_CUDA(cudaStreamSynchronize(st));
+        g->P = 0;
+        G.P = 0;
+        *out = g;
+        return TM_OK;
+    }
+
+    // ---- scratch: keys/values for three sorts (double-buffered) + pair scan
+    uint32_t *ks, *kd, *va, *vb, *kt, *vt;
+    int64_t *head, *pid, *dP;
+    size_t scratch = 6 * align256(4 * M) + 2 * sz_i64m + 256;
+    char* sb = nullptr;
+    e = cudaMallocAsync((void**)&sb, scratch, st);
+    if (e != cudaSuccess) {
+        cudaFree(g->block);
+        delete g;
+        return cuda_status(e, "cudaMallocAsync(graph scratch)", __FILE__, __LINE__);
+    }
+    char* q = sb;
+    auto takes = [&](size_t bytes) { char* r = q; q += align256(bytes); return (void*)r; };
+    ks = (uint32_t*)takes(4 * M);
+    kd = (uint32_t*)takes(4 * M);
+    va = (uint32_t*)takes(4 * M);
+    vb = (uint32_t*)takes(4 * M);
+    kt = (uint32_t*)takes(4 * M);
+    vt = (uint32_t*)takes(4 * M);
+    head = (int64_t*)takes(8 * M);
+    pid = (int64_t*)takes(8 * M);
+    dP = (int64_t*)takes(8);
+
+    int bits = bits_for(n);
+    unsigned gr = grid_for(m);
+    k_ingest<<<gr, kThreads, 0, st>>>(d_src, d_dst, d_t, m, tmin, gs, gd, gt, ks, kd, va, vb); count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+    // out view: edges stably sorted by source (time order kept inside a source)
+    if (rc == TM_OK) rc = radix_sort_pairs(ks, va, kt, vt, m, bits, st);
+    if (rc == TM_OK) {
+        k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(ks, m, n, out_off); count_launch();
+        k_gather_view<<<gr, kThreads, 0, st>>>(va, gd, gt, m, out_nbr, out_t); count_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+    }
+    // in view: stably sorted by destination
+    if (rc == TM_OK) rc = radix_sort_pairs(kd, vb, kt, vt, m, bits, st);
+    if (rc == TM_OK) {
+        k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kd, m, n, in_off); count_launch();
+        k_gather_view<<<gr, kThreads, 0, st>>>(vb, gs, gt, m, in_nbr, in_t); count_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+    }
+    // pair view: the in-view order stably re-sorted by source = (src, dst, time)
+    if (rc == TM_OK) {
+        k_gather_view<<<gr, kThreads, 0, st>>>(vb, gs, gt, m, (int32_t*)ks, (int64_t*)head); count_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+    }
+    if (rc == TM_OK) rc = radix_sort_pairs(ks, vb, kt, vt, m, bits, st);
+    if (rc == TM_OK) {
+        k_pair_heads<<<gr, kThreads, 0, st>>>(vb, gs, gd, gt, m, head, pair_t); count_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+    }
+    if (rc == TM_OK) rc = scan_exclusive_i64(head, pid, m, dP, st);
+    if (rc == TM_OK) {
+        k_pair_index<<<gr, kThreads, 0, st>>>(vb, gd, head, pid, m, pair_dst, pair_off); count_launch();
+        k_pair_tail<<<1, 1, 0, st>>>(pair_off, dP, m); count_launch();
+        k_pk_off<<<grid_for((int64_t)n + 1), kThreads, 0, st>>>(out_off, head, pid, dP, m, n, pk_off); count_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+    }
+    int64_t P = 0;
+    if (rc == TM_OK) {
+        e = cudaMemcpyAsync(&P, dP, 8, cudaMemcpyDeviceToHost, st);
+        int ev1 = pe.mark(st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_status(e, "graph build", __FILE__, __LINE__);
+        if (rc == TM_OK && pe.on) store_profile_graph(pe.ms(ev0, ev1));
+    }
+    cudaFreeAsync(sb, st);
+    if (rc != TM_OK) {
+        cudaStreamSynchronize(st);
+        cudaFree(g->block);
+        delete g;
+        return rc;
+    }
+    g->P = P;
+    G.P = P;
+    *out = g;
+    return TM_OK;
+}
+
+}  // namespace
+}  // namespace tmo
+
+extern "C" {
+
+int tm_graph_load_device(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, int64_t m,
+                         int32_t n_nodes, void* stream, tm_graph** out) {
+    return tmo::build_graph(d_src, d_dst, d_t, m, n_nodes, (cudaStream_t)stream, out);
+}
+
+int tm_graph_load(const int32_t* src, const int32_t* dst, const int64_t* t, int64_t m,
+                  int32_t n_nodes, tm_graph** out) {
+    if (!out) { tmo::set_error("out is NULL"); return TM_EINVAL; }
+    *out = nullptr;
+    if (m < 0 || m >= ((int64_t)1 << 31) - 1) { tmo::set_error("m outside [0, 2^31-1)"); return TM_EINVAL; }
+    if (m > 0 && (!src || !dst || !t)) { tmo::set_error("NULL edge array"); return TM_EINVAL; }
+    cudaStream_t st;
+    TM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int32_t *ds = nullptr, *dd = nullptr;
+    int64_t* dt = nullptr;
+    size_t M = (size_t)(m > 0 ? m : 1);
+    int rc = TM_OK;
+    cudaError_t e = cudaMallocAsync((void**)&ds, 4 * M, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&dd, 4 * M, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&dt, 8 * M, st);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(ds, src, 4 * (size_t)m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(dd, dst, 4 * (size_t)m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(dt, t, 8 * (size_t)m, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = tmo::cuda_status(e, "tm_graph_load copy", __FILE__, __LINE__);
+    if (rc == TM_OK) rc = tmo::build_graph(ds, dd, dt, m, n_nodes, st, out);
+    cudaFreeAsync(ds, st);
+    cudaFreeAsync(dd, st);
+    cudaFreeAsync(dt, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+}
+
+void tm_graph_free(tm_graph* g) {
+    if (!g) return;
+    if (g->block) cudaFree(g->block);
+    delete g;
+}
+
+int tm_graph_get_info(const tm_graph* g, tm_graph_info* info) {
+    if (!g || !info) { tmo::set_error("NULL argument"); return TM_EINVAL; }
+    std::memset(info, 0, sizeof(*info));
+    info->m = g->m;
+    info->n_nodes = g->n;
+    info->n_pairs = g->P;
+    info->t_min = g->t_min;
+    info->t_max = g->t_max;
+    info->device_bytes = g->bytes;
+    return TM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1010 @@
+// The estimator's hot path (Algorithm 1 around the exact counter A of
+// Section 4), one batch of queries at a time:
+//
+//   k_wtab     per estimate query, the weights 1/p_{M'} = c delta / (c delta - Delta)
+//              (Eq. 2) for every duration Delta in [0, delta], in unsigned Q64
+//              fixed point, so that window sums are exact integer sums.
+//   k_windows  one thread per window I_j of Eq. 1 of every shift of every
+//              query: shift s and keep decision U_j < q_j (Algorithm 1), and
+//              T_j as an edge range [lo, hi) found by binary search on time.
+//   k_level2   one thread per first edge of every kept window: the range of
+//              candidates for the second motif edge (time in (t_1, t_1 + delta],
+//              clamped to the window) in the adjacency view the motif needs.
+//   k_match    persistent warps over equal chunks of the concatenated
+//              second-edge candidates (the work queue); deeper motif edges are
+//              expanded warp-cooperatively (range lengths scanned across the
+//              warp, each lane takes one candidate, owner found by shuffles);
+//              in exact mode the last motif edge is counted by range length.
+//   k_fold     per query: Z_k = sum_j W_j / q_j per shift and the mean over
+//              shifts (Algorithm 1's return value).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tm_internal.cuh"
+
+namespace tmo {
+
+Tuning& tuning() {
+    static Tuning t;
+    return t;
+}
+
+namespace {
+
+constexpr int64_t kInf = INT64_MAX;
+constexpr int64_t kWtabMax = (int64_t)1 << 22;   // largest delta+1 given a weight table
+
+// per-window accumulator fields
+enum { A_COUNT = 0, A_WLO, A_WHI, A_FIRST, A_CAND, A_LAST, A_INST, A_N };
+
+struct WinDev {
+    int64_t* lo;      // T_j = edges [lo, hi)
+    int64_t* hi;
+    int64_t* tend;    // last admissible time (window end), kInf for exact
+    int64_t* start;   // a_j
+    int64_t* j;       // window index (1-based; 0 for exact)
+    int32_t* q;       // query
+    int32_t* k;       // shift index
+    int32_t* kept;
+    double* qj;       // q_j
+    int64_t* nfirst;  // hi - lo if kept else 0
+    int64_t* fbase;   // exclusive scan of nfirst
+    unsigned long long* acc;  // [NW][A_N]
+};
+
+struct MatchArgs {
+    GraphDev G;
+    const QPlan* plans;
+    int nq;
+    WinDev W;
+    int64_t NW;
+    int64_t F;
+    const int32_t* fwin;   // [F] window of each first edge
+    const int64_t* lo2;    // [F] start of its second-edge candidate range
+    const int64_t* excl;   // [F] exclusive scan of the range lengths
+    const int64_t* d_W2;   // total second-edge candidates
+    unsigned long long* counter;
+    int64_t chunk;
+    int enum_threshold;
+};
+
+// ----------------------------------------------------------------- helpers
+template <int K>
+__device__ __forceinline__ int32_t phi_get(const int32_t (&phi)[K], int idx) {
+    int32_t v = phi[0];
+#pragma unroll
+    for (int i = 1; i < K; i++)
+        if (idx == i) v = phi[i];
+    return v;
+}
+template <int K>
+__device__ __forceinline__ void phi_set(int32_t (&phi)[K], int idx, int32_t v) {
+#pragma unroll
+    for (int i = 0; i < K; i++)
+        if (idx == i) phi[i] = v;
+}
+template <int K>
+__device__ __forceinline__ bool phi_has(const int32_t (&phi)[K], int nb, int32_t v) {
+    bool r = false;
+#pragma unroll
+    for (int i = 0; i < K; i++) r |= (i < nb) & (phi[i] == v);
+    return r;
+}
+
+// time-sorted entries of the (u -> v) pair: [a, b) of pair_t
+__device__ __forceinline__ bool pair_segment(const GraphDev& G, int32_t u, int32_t v, int64_t& a,
+                                             int64_t& b) {
+    int64_t lo = __ldg(G.pk_off + u), hi = __ldg(G.pk_off + u + 1);
+    int64_t p = lower_bound_i32(G.pair_dst, lo, hi, v);
+    if (p < hi && __ldg(G.pair_dst + p) == v) {
+        a = __ldg(G.pair_off + p);
+        b = __ldg(G.pair_off + p + 1);
+        return true;
+    }
+    a = b = 0;
+    return false;
+}
+
+__device__ __forceinline__ int64_t pair_count(const GraphDev& G, int32_t u, int32_t v, int64_t tprev,
+                                              int64_t thi) {
+    int64_t a, b;
+    if (!pair_segment(G, u, v, a, b)) return 0;
+    int64_t lo = upper_bound_i64(G.pair_t, a, b, tprev);
+    int64_t hi = upper_bound_i64(G.pair_t, lo, b, thi);
+    return hi - lo;
+}
+
+// candidates of motif edge P given the bound nodes: entries [lo, lo+len) of
+// the view's time array with time in (tprev, thi]
+template <int K>
+__device__ __forceinline__ void level_range(const GraphDev& G, const LevelPlan& P,
+                                            const int32_t (&phi)[K], int64_t tprev, int64_t thi,
+                                            int64_t& lo, int64_t& len) {
+    const int64_t* ta;
+    int64_t a, b;
+    if (P.view == kPair) {
+        ta = G.pair_t;
+        if (!pair_segment(G, phi_get(phi, P.su), phi_get(phi, P.sv), a, b)) { lo = 0; len = 0; return; }
+    } else if (P.view == kOut) {
+        int32_t u = phi_get(phi, P.su);
+        ta = G.out_t; a = __ldg(G.out_off + u); b = __ldg(G.out_off + u + 1);
+    } else if (P.view == kIn) {
+        int32_t v = phi_get(phi, P.sv);
+        ta = G.in_t; a = __ldg(G.in_off + v); b = __ldg(G.in_off + v + 1);
+    } else {
+        ta = G.t; a = 0; b = G.m;
+    }
+    if (thi <= tprev) { lo = a; len = 0; return; }
+    lo = upper_bound_i64(ta, a, b, tprev);
+    int64_t hi = upper_bound_i64(ta, lo, b, thi);
+    len = hi - lo;
+}
+
+// read candidate c of the view; returns its (src, dst, time)
+template <int K>
+__device__ __forceinline__ void read_cand(const GraphDev& G, const LevelPlan& P,
+                                          const int32_t (&phi)[K], int64_t c, int32_t& s,
+                                          int32_t& d, int64_t& tc) {
+    if (P.view == kPair) {
+        s = phi_get(phi, P.su); d = phi_get(phi, P.sv); tc = __ldg(G.pair_t + c);
+    } else if (P.view == kOut) {
+        s = phi_get(phi, P.su); d = __ldg(G.out_nbr + c); tc = __ldg(G.out_t + c);
+    } else if (P.view == kIn) {
+        s = __ldg(G.in_nbr + c); d = phi_get(phi, P.sv); tc = __ldg(G.in_t + c);
+    } else {
+        s = __ldg(G.src + c); d = __ldg(G.dst + c); tc = __ldg(G.t + c);
+    }
+}
+
+// injectivity of the node map (Def. 2.2 item 1) for a candidate, and binding
+template <int K>
+__device__ __forceinline__ bool check_bind(const LevelPlan& P, int32_t (&phi)[K], int32_t s,
+                                           int32_t d) {
+    if (s == d) return false;
+    if (P.bind_u && phi_has(phi, P.nb, s)) return false;
+    if (P.bind_v && phi_has(phi, P.nb, d)) return false;
+    if (P.bind_u) phi_set(phi, P.su, s);
+    if (P.bind_v) phi_set(phi, P.sv, d);
+    return true;
+}
+
+// exact count of the last motif edge's candidates in (tprev, thi] when one
+// endpoint is new: the range length minus the entries whose new endpoint is
+// already bound (those are exactly the pair segments to bound nodes)
+template <int K>
+__device__ __forceinline__ int64_t last_count_subtract(const GraphDev& G, const LevelPlan& P,
+                                                       const int32_t (&phi)[K], int64_t len,
+                                                       int64_t tprev, int64_t thi) {
+    int64_t excl = 0;
+    if (P.view == kOut) {
+        int32_t u = phi_get(phi, P.su);
+#pragma unroll
+        for (int i = 0; i < K; i++)
+            if (i < P.nb) excl += pair_count(G, u, phi[i], tprev, thi);
+    } else {
+        int32_t v = phi_get(phi, P.sv);
+#pragma unroll
+        for (int i = 0; i < K; i++)
+            if (i < P.nb) excl += pair_count(G, phi[i], v, tprev, thi);
+    }
+    return len - excl;
+}
+
+struct Acc {
+    int64_t win;
+    unsigned long long f[A_N];
+};
+
+__device__ __forceinline__ void acc_zero(Acc& a) {
+#pragma unroll
+    for (int i = 0; i < A_N; i++) a.f[i] = 0;
+}
+
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* lo_hi, unsigned long long lo,
+                                                unsigned long long hi) {
+    if (lo) {
+        unsigned long long old = atomicAdd(lo_hi, lo);
+        if (old + lo < old) hi += 1;
+    }
+    if (hi) atomicAdd(lo_hi + 1, hi);
+}
+
+__device__ __forceinline__ void acc_flush_lane(Acc& a, unsigned long long* acc) {
+    if (a.win < 0) return;
+    unsigned long long* p = acc + a.win * A_N;
+    if (a.f[A_COUNT]) atomicAdd(p + A_COUNT, a.f[A_COUNT]);
+    atomic_add_u128(p + A_WLO, a.f[A_WLO], a.f[A_WHI]);
+#pragma unroll
+    for (int i = A_FIRST; i < A_N; i++)
+        if (a.f[i]) atomicAdd(p + i, a.f[i]);
+    acc_zero(a);
+}
+
+// warp-uniform flush: one set of atomics when every lane holds the same window
+__device__ __forceinline__ void acc_flush_warp(Acc& a, unsigned long long* acc) {
+    int64_t w0 = __shfl_sync(kFull, a.win, 0);
+    if (__all_sync(kFull, a.win == w0 || a.win < 0) && w0 >= 0) {
+        // reduce: Q64 weights carried as 128-bit via (lo, hi) with carries
+        unsigned long long lo = a.f[A_WLO], hi = a.f[A_WHI];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long lo2 = __shfl_xor_sync(kFull, lo, o);
+            unsigned long long hi2 = __shfl_xor_sync(kFull, hi, o);
+            unsigned long long s = lo + lo2;
+            hi = hi + hi2 + (s < lo ? 1ull : 0ull);
+            lo = s;
+        }
+        unsigned long long v[A_N];
+#pragma unroll
+        for (int i = 0; i < A_N; i++) {
+            v[i] = a.f[i];
+            if (i == A_WLO || i == A_WHI) continue;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(kFull, v[i], o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long* p = acc + w0 * A_N;
+            if (v[A_COUNT]) atomicAdd(p + A_COUNT, v[A_COUNT]);
+            atomic_add_u128(p + A_WLO, lo, hi);
+#pragma unroll
+            for (int i = A_FIRST; i < A_N; i++)
+                if (v[i]) atomicAdd(p + i, v[i]);
+        }
+        acc_zero(a);
+    } else {
+        acc_flush_lane(a, acc);
+    }
+}
+
+__device__ __forceinline__ void acc_switch(Acc& a, int64_t win, unsigned long long* acc) {
+    if (a.win != win) {
+        acc_flush_lane(a, acc);
+        a.win = win;
+    }
+}
+
+__device__ __forceinline__ void add_weight(Acc& a, const QPlan& Q, int64_t dur) {
+    unsigned long long wi, wf;
+    if (Q.wtab) {
+        wi = __ldg(Q.wtab + 2 * dur);
+        wf = __ldg(Q.wtab + 2 * dur + 1);
+    } else {
+        // c delta / (c delta - dur) by long division, 64 fraction bits
+        unsigned long long D = (unsigned long long)(Q.cd - dur);
+        unsigned long long N = (unsigned long long)Q.cd;
+        wi = N / D;
+        unsigned long long r = N - wi * D;
+        wf = 0;
+        for (int i = 0; i < 64; i++) {
+            r <<= 1;
+            wf <<= 1;
+            if (r >= D) { r -= D; wf |= 1; }
+        }
+    }
+    unsigned long long s = a.f[A_WLO] + wf;
+    a.f[A_WHI] += wi + (s < wf ? 1ull : 0ull);
+    a.f[A_WLO] = s;
+}
+
+__device__ __forceinline__ int64_t warp_incl_scan64(int64_t v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// ----------------------------------------------------------------- kernels
+__global__ void k_wtab(uint64_t* __restrict__ tab, int64_t delta, int64_t cd) {
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d <= delta;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long D = (unsigned long long)(cd - d);
+        if (D == 0) {  // duration c*delta (c = 1) never fits inside a window of c*delta ticks
+            tab[2 * d] = 0;
+            tab[2 * d + 1] = 0;
+            continue;
+        }
+        unsigned long long N = (unsigned long long)cd;
+        unsigned long long wi = N / D, r = N - wi * D, wf = 0;
+        for (int i = 0; i < 64; i++) {
+            r <<= 1;
+            wf <<= 1;
+            if (r >= D) { r -= D; wf |= 1; }
+        }
+        tab[2 * d] = wi;
+        tab[2 * d + 1] = wf;
+    }
+}
+
+__global__ void k_windows(GraphDev G, const QPlan* __restrict__ plans, int nq, WinDev W, int64_t NW) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < NW;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        int lo_q = 0, hi_q = nq;
+        while (hi_q - lo_q > 1) {
+            int mid = (lo_q + hi_q) >> 1;
+            if (plans[mid].win_base <= w) lo_q = mid; else hi_q = mid;
+        }
+        const QPlan& Q = plans[lo_q];
+        int64_t r = w - Q.win_base;
+        int64_t lo, hi, tend, start, j;
+        int32_t k, kept;
+        double qj;
+        if (Q.mode == TM_MODE_EXACT) {
+            k = 0; j = 0; start = 0; lo = 0; hi = G.m; tend = kInf; kept = 1; qj = 1.0;
+        } else {
+            k = (int32_t)(r / Q.J);
+            j = r % Q.J + 1;
+            uint64_t h0 = draw(Q.seed, (uint64_t)k, 0);
+            int64_t s = -(int64_t)(h0 % (uint64_t)Q.cd);
+            start = s + (j - 1) * Q.cd;
+            tend = start + Q.cd - 1;
+            lo = lower_bound_i64(G.t, 0, G.m, start);
+            hi = upper_bound_i64(G.t, lo, G.m, tend);
+            if (Q.q_mode == TM_Q_EDGES) {
+                qj = G.m > 0 ? Q.p * (double)(hi - lo) / (double)G.m : 0.0;
+                if (qj > 1.0) qj = 1.0;
+            } else {
+                qj = Q.p;
+            }
+            double u = (double)(draw(Q.seed, (uint64_t)k, (uint64_t)j) >> 11) * 0x1.0p-53;
+            kept = u < qj ? 1 : 0;
+        }
+        W.lo[w] = lo; W.hi[w] = hi; W.tend[w] = tend; W.start[w] = start; W.j[w] = j;
+        W.q[w] = lo_q; W.k[w] = k; W.kept[w] = kept; W.qj[w] = qj;
+        W.nfirst[w] = kept ? hi - lo : 0;
+    }
+}
+
+// one warp-uniform grid-stride loop over first edges f
+__global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict__ fwin,
+                                                int64_t* __restrict__ len2, int64_t* __restrict__ lo2) {
+    const GraphDev& G = A.G;
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    Acc acc;
+    acc.win = -1;
+    acc_zero(acc);
+    for (int64_t base = warp * 32; base < A.F; base += nwarps * 32) {
+        int64_t f = base + lane;
+        bool valid = f < A.F;
+        int64_t wi = -1;
+        if (valid) {
+            int64_t lo = 0, hi = A.NW;
+            // last window whose fbase <= f
+            while (hi - lo > 1) {
+                int64_t mid = (lo + hi) >> 1;
+                if (__ldg(A.W.fbase + mid) <= f) lo = mid; else hi = mid;
+            }
+            wi = lo;
+        }
+        // flush when any lane changes window
+        if (__any_sync(kFull, valid && acc.win != wi)) {
+            acc_flush_warp(acc, A.W.acc);
+            if (valid) acc.win = wi;
+        }
+        if (!valid) continue;
+        const QPlan& Q = A.plans[A.W.q[wi]];
+        int64_t e1 = A.W.lo[wi] + (f - A.W.fbase[wi]);
+        int32_t s1 = __ldg(G.src + e1), d1 = __ldg(G.dst + e1);
+        int64_t t1 = __ldg(G.t + e1);
+        int64_t thi = min(t1 + Q.delta, A.W.tend[wi]);
+        int64_t len = 0, lo = 0;
+        acc.f[A_FIRST] += 1;
+        if (s1 != d1) {
+            if (Q.l == 1) {
+                acc.f[A_COUNT] += 1;
+                if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, 0);
+            } else {
+                int32_t phi[TM_K_MAX];
+#pragma unroll
+                for (int i = 0; i < TM_K_MAX; i++) phi[i] = -1;
+                phi[0] = s1;
+                phi[1] = d1;
+                const LevelPlan P = Q.lv[1];
+                level_range(G, P, phi, t1, thi, lo, len);
+                if (Q.l == 2 && Q.mode == TM_MODE_EXACT) {
+                    if (P.view == kPair) {
+                        acc.f[A_COUNT] += len;
+                        acc.f[A_LAST] += 1;
+                        len = 0;
+                    } else if (len > A.enum_threshold && P.view != kAll) {
+                        acc.f[A_COUNT] += last_count_subtract(G, P, phi, len, t1, thi);
+                        acc.f[A_LAST] += 1;
+                        len = 0;
+                    }
+                }
+            }
+        }
+        fwin[f] = (int32_t)wi;
+        len2[f] = len;
+        lo2[f] = lo;
+    }
+    acc_flush_warp(acc, A.W.acc);
+}
+
+// Warp-cooperative expansion of motif edge D (0-based) for the 32 partial
+// instances held by the lanes (valid ones have edges 0..D-1 matched).
+template <int D, int LMAX>
+__device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
+                       int32_t (&phi)[TM_K_MAX], int64_t t1, int64_t tprev, int64_t thi, Acc& acc) {
+    const GraphDev& G = A.G;
+    int lane = threadIdx.x & 31;
+    int64_t lo = 0, len = 0;
+    if (valid) {
+        const QPlan& Q = A.plans[q];
+        const LevelPlan P = Q.lv[D];
+        level_range(G, P, phi, tprev, thi, lo, len);
+        if (D == Q.l - 1) {
+            acc_switch(acc, win, A.W.acc);
+            acc.f[A_LAST] += 1;
+            if (Q.mode == TM_MODE_EXACT) {
+                if (P.view == kPair) {
+                    acc.f[A_COUNT] += len;
+                    len = 0;
+                } else if (len > A.enum_threshold && P.view != kAll) {
+                    acc.f[A_COUNT] += last_count_subtract(G, P, phi, len, tprev, thi);
+                    len = 0;
+                }
+            }
+        }
+    }
+    int64_t incl = warp_incl_scan64(len);
+    int64_t total = __shfl_sync(kFull, incl, 31);
+    int64_t mystart = incl - len;
+    for (int64_t base = 0; base < total; base += 32) {
+        int64_t x = base + lane;
+        bool has = x < total;
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            int64_t v = __shfl_sync(kFull, incl, o + step - 1);
+            if (v <= x) o += step;
+        }
+        if (!has) o = 0;
+        int32_t oq = __shfl_sync(kFull, q, o);
+        int64_t ow = __shfl_sync(kFull, win, o);
+        int64_t olo = __shfl_sync(kFull, lo, o);
+        int64_t ost = __shfl_sync(kFull, mystart, o);
+        int64_t ot1 = __shfl_sync(kFull, t1, o);
+        int64_t othi = __shfl_sync(kFull, thi, o);
+        int32_t ophi[TM_K_MAX];
+#pragma unroll
+        for (int i = 0; i < TM_K_MAX; i++) ophi[i] = __shfl_sync(kFull, phi[i], o);
+        bool ok = false, deeper = false;
+        int64_t tc = 0;
+        if (has) {
+            const QPlan& Q = A.plans[oq];
+            const LevelPlan P = Q.lv[D];
+            int32_t s, d;
+            read_cand(G, P, ophi, olo + (x - ost), s, d, tc);
+            ok = check_bind(P, ophi, s, d);
+            if (D == Q.l - 1) {
+                acc_switch(acc, ow, A.W.acc);
+                acc.f[A_INST] += 1;
+                if (ok) {
+                    acc.f[A_COUNT] += 1;
+                    if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - ot1);
+                }
+            } else {
+                acc_switch(acc, ow, A.W.acc);
+                acc.f[A_CAND] += 1;
+                deeper = ok;
+            }
+        }
+        if constexpr (D + 1 < LMAX) {
+            if (__any_sync(kFull, deeper))
+                expand<D + 1, LMAX>(A, deeper, oq, ow, ophi, ot1, tc, othi, acc);
+        }
+    }
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(256) k_match(MatchArgs A) {
+    const GraphDev& G = A.G;
+    int lane = threadIdx.x & 31;
+    int64_t W2 = *A.d_W2;
+    Acc acc;
+    acc.win = -1;
+    acc_zero(acc);
+    for (;;) {
+        unsigned long long c0u = 0;
+        if (lane == 0) c0u = atomicAdd(A.counter, (unsigned long long)A.chunk);
+        int64_t c0 = (int64_t)__shfl_sync(kFull, c0u, 0);
+        if (c0 >= W2) break;
+        int64_t c1 = min(c0 + A.chunk, W2);
+        int64_t fb = 0, fe = 0;
+        if (lane < 2) {
+            int64_t key = lane == 0 ? c0 : c1 - 1;
+            fb = upper_bound_i64(A.excl, 0, A.F, key) - 1;
+        }
+        fe = __shfl_sync(kFull, fb, 1);
+        fb = __shfl_sync(kFull, fb, 0);
+        for (int64_t base = c0; base < c1; base += 32) {
+            int64_t w = base + lane;
+            bool valid = w < c1;
+            int32_t q = 0;
+            int64_t win = -1, t1 = 0, thi = 0, tc = 0;
+            int32_t phi[TM_K_MAX];
+#pragma unroll
+            for (int i = 0; i < TM_K_MAX; i++) phi[i] = -1;
+            bool deeper = false;
+            if (valid) {
+                int64_t f = upper_bound_i64(A.excl, fb, fe + 1, w) - 1;
+                win = A.fwin[f];
+                q = A.W.q[win];
+                const QPlan& Q = A.plans[q];
+                int64_t e1 = A.W.lo[win] + (f - A.W.fbase[win]);
+                phi[0] = __ldg(G.src + e1);
+                phi[1] = __ldg(G.dst + e1);
+                t1 = __ldg(G.t + e1);
+                thi = min(t1 + Q.delta, A.W.tend[win]);
+                const LevelPlan P = Q.lv[1];
+                int32_t s, d;
+                read_cand(G, P, phi, A.lo2[f] + (w - A.excl[f]), s, d, tc);
+                bool ok = check_bind(P, phi, s, d);
+                acc_switch(acc, win, A.W.acc);
+                if (Q.l == 2) {
+                    acc.f[A_INST] += 1;
+                    if (ok) {
+                        acc.f[A_COUNT] += 1;
+                        if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - t1);
+                    }
+                } else {
+                    acc.f[A_CAND] += 1;
+                    deeper = ok;
+                }
+            }
+            if (__any_sync(kFull, deeper))
+                expand<2, LMAX>(A, deeper, q, win, phi, t1, tc, thi, acc);
+        }
+        acc_flush_warp(acc, A.W.acc);
+    }
+    acc_flush_warp(acc, A.W.acc);
+}
+
+// per query: sums over its windows, per shift; Z_k and the mean (Algorithm 1)
+__global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __restrict__ res) {
+    int qi = blockIdx.x;
+    const QPlan& Q = plans[qi];
+    __shared__ double sh_d[2][32];
+    __shared__ unsigned long long sh_u[A_N + 1][32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t nwin = Q.mode == TM_MODE_EXACT ? 1 : Q.J;
+    int nsh = Q.mode == TM_MODE_EXACT ? 1 : Q.b;
+    if (Q.l <= 0) nsh = 0;   // query rejected on the host
+    double zsum = 0.0, vsum = 0.0;
+    unsigned long long tot[A_N + 1] = {0};   // + kept windows
+    int overflow = 0;
+    for (int k = 0; k < nsh; k++) {
+        unsigned long long s[A_N + 1] = {0};
+        double zq = 0.0, vq = 0.0;
+        unsigned long long wlo = 0, whi = 0;
+        for (int64_t r = threadIdx.x; r < nwin; r += blockDim.x) {
+            int64_t w = Q.win_base + (int64_t)k * nwin + r;
+            if (!W.kept[w]) continue;
+            const unsigned long long* a = W.acc + w * A_N;
+            s[A_COUNT] += a[A_COUNT];
+            for (int i = A_FIRST; i < A_N; i++) s[i] += a[i];
+            s[A_N] += 1;
+            unsigned long long x = wlo + a[A_WLO];
+            whi += a[A_WHI] + (x < wlo ? 1ull : 0ull);
+            wlo = x;
+            double y = (double)a[A_WHI] + (double)a[A_WLO] * 0x1.0p-64;
+            double qj = W.qj[w];
+            if (Q.q_mode == TM_Q_EDGES) zq += y / qj;
+            vq += y * y * (1.0 - qj) / (qj * qj);
+        }
+        // block reduce integer fields and the 128-bit weight
+        for (int o = 16; o > 0; o >>= 1) {
+            for (int i = 0; i <= A_N; i++)
+                if (i != A_WLO && i != A_WHI) s[i] += __shfl_xor_sync(kFull, s[i], o);
+            unsigned long long l2 = __shfl_xor_sync(kFull, wlo, o);
+            unsigned long long h2 = __shfl_xor_sync(kFull, whi, o);
+            unsigned long long x = wlo + l2;
+            whi = whi + h2 + (x < wlo ? 1ull : 0ull);
+            wlo = x;
+            zq += __shfl_xor_sync(kFull, zq, o);
+            vq += __shfl_xor_sync(kFull, vq, o);
+        }
+        s[A_WLO] = wlo;
+        s[A_WHI] = whi;
+        __syncthreads();
+        if (lane == 0) {
+            for (int i = 0; i <= A_N; i++) sh_u[i][wid] = s[i];
+            sh_d[0][wid] = zq;
+            sh_d[1][wid] = vq;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long u[A_N + 1] = {0};
+            double z2 = 0.0, v2 = 0.0;
+            unsigned long long L = 0, H = 0;
+            for (int ww = 0; ww < nw; ww++) {
+                for (int i = 0; i <= A_N; i++)
+                    if (i != A_WLO && i != A_WHI) u[i] += sh_u[i][ww];
+                unsigned long long x = L + sh_u[A_WLO][ww];
+                H += sh_u[A_WHI][ww] + (x < L ? 1ull : 0ull);
+                L = x;
+                z2 += sh_d[0][ww];
+                v2 += sh_d[1][ww];
+            }
+            if (H >= (1ull << 63) || u[A_COUNT] >= (1ull << 63)) overflow = 1;
+            for (int i = 0; i <= A_N; i++)
+                if (i != A_WLO && i != A_WHI) tot[i] += u[i];
+            double Wd = (double)H + (double)L * 0x1.0p-64;
+            double zk = Q.q_mode == TM_Q_EDGES ? z2 : Wd / Q.p;
+            zsum += zk;
+            vsum += v2;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        tm_result r;
+        memset(&r, 0, sizeof(r));
+        r.status = Q.l <= 0 ? -1 : (overflow ? TM_EOVERFLOW : TM_OK);
+        r.count = (int64_t)tot[A_COUNT];
+        if (Q.mode == TM_MODE_EXACT) {
+            r.estimate = (double)tot[A_COUNT];
+            r.windows = 1;
+            r.windows_kept = 1;
+            r.var_hat = 0.0;
+        } else {
+            r.estimate = nsh ? zsum / nsh : 0.0;
+            r.windows = (int64_t)nsh * Q.J;
+            r.windows_kept = (int64_t)tot[A_N];
+            r.var_hat = nsh ? vsum / nsh : 0.0;
+        }
+        r.first_edges = (int64_t)tot[A_FIRST];
+        r.cand_edges = (int64_t)tot[A_CAND];
+        r.last_ranges = (int64_t)tot[A_LAST];
+        r.inst_read = (int64_t)tot[A_INST];
+        res[qi] = r;
+    }
+}
+
+// ------------------------------------------------------- plain baseline K10
+template <int D, int LMAX>
+__device__ int64_t plain_dfs(const GraphDev& G, const QPlan& Q, int32_t (&phi)[TM_K_MAX],
+                             int64_t tprev, int64_t thi) {
+    const LevelPlan P = Q.lv[D];
+    int64_t lo, len;
+    level_range(G, P, phi, tprev, thi, lo, len);
+    if (D == Q.l - 1 && P.view == kPair) return len;
+    int64_t c = 0;
+    for (int64_t i = 0; i < len; i++) {
+        int32_t s, d;
+        int64_t tc;
+        int32_t nphi[TM_K_MAX];
+#pragma unroll
+        for (int z = 0; z < TM_K_MAX; z++) nphi[z] = phi[z];
+        read_cand(G, P, nphi, lo + i, s, d, tc);
+        if (!check_bind(P, nphi, s, d)) continue;
+        if (D == Q.l - 1) {
+            c += 1;
+        } else if constexpr (D + 1 < LMAX) {
+            c += plain_dfs<D + 1, LMAX>(G, Q, nphi, tc, thi);
+        }
+    }
+    return c;
+}
+
+__global__ void k_plain(GraphDev G, const QPlan* __restrict__ plan, unsigned long long* out) {
+    const QPlan& Q = *plan;
+    unsigned long long c = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < G.m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s1 = G.src[e], d1 = G.dst[e];
+        if (s1 == d1) continue;
+        if (Q.l == 1) { c += 1; continue; }
+        int32_t phi[TM_K_MAX];
+#pragma unroll
+        for (int i = 0; i < TM_K_MAX; i++) phi[i] = -1;
+        phi[0] = s1;
+        phi[1] = d1;
+        int64_t t1 = G.t[e];
+        c += (unsigned long long)plain_dfs<1, TM_L_MAX>(G, Q, phi, t1, t1 + Q.delta);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// --------------------------------------------------------------- host side
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int validate_query(const tm_graph* g, const tm_query& q, std::string& why) {
+    if (!q.motif) { why = "motif is NULL"; return TM_EINVAL; }
+    if (q.delta < 0) { why = "delta < 0"; return TM_EINVAL; }
+    if (q.delta >= ((int64_t)1 << 61)) { why = "delta >= 2^61"; return TM_EINVAL; }
+    if (q.mode != TM_MODE_EXACT && q.mode != TM_MODE_ESTIMATE) { why = "bad mode"; return TM_EINVAL; }
+    if (q.mode == TM_MODE_ESTIMATE) {
+        if (q.delta < 1) { why = "estimate needs delta >= 1"; return TM_EINVAL; }
+        if (q.c < 1) { why = "c < 1"; return TM_EINVAL; }
+        if (q.b < 1 || q.b > (1 << 20)) { why = "b outside [1, 2^20]"; return TM_EINVAL; }
+        if (q.q_mode != TM_Q_UNIFORM && q.q_mode != TM_Q_EDGES) { why = "bad q_mode"; return TM_EINVAL; }
+        if (q.q_mode == TM_Q_UNIFORM && !(q.p > 0.0 && q.p <= 1.0)) { why = "p outside (0, 1]"; return TM_EINVAL; }
+        if (q.q_mode == TM_Q_EDGES && !(q.p > 0.0 && std::isfinite(q.p))) { why = "r must be > 0"; return TM_EINVAL; }
+        __int128 cd = (__int128)q.c * q.delta;
+        if (cd >= ((__int128)1 << 61)) { why = "c*delta >= 2^61"; return TM_EINVAL; }
+        int64_t J = 1 + (g->t_max + (int64_t)cd - 1) / (int64_t)cd;
+        if ((__int128)J * q.b > ((__int128)1 << 31)) { why = "too many windows (b * J > 2^31)"; return TM_EINVAL; }
+    }
+    return TM_OK;
+}
+
+void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
+    std::memset(&P, 0, sizeof(P));
+    const tm_motif* m = q.motif;
+    P.l = m->l;
+    P.k = m->k;
+    P.mode = q.mode;
+    P.delta = q.delta;
+    for (int i = 0; i < TM_L_MAX; i++) P.lv[i] = m->lv[i];
+    if (q.mode == TM_MODE_EXACT) {
+        P.b = 1; P.cd = 0; P.J = 1; P.p = 1.0; P.q_mode = TM_Q_UNIFORM;
+    } else {
+        P.b = q.b;
+        P.cd = (int64_t)q.c * q.delta;
+        P.J = 1 + (g->t_max + P.cd - 1) / P.cd;
+        P.p = q.p;
+        P.seed = q.seed;
+        P.q_mode = q.q_mode;
+    }
+}
+
+}  // namespace
+
+int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
+              BatchOut* dbg) {
+    if (!g || (!qs && nq > 0) || (!res && nq > 0) || nq < 0) { set_error("NULL argument"); return TM_EINVAL; }
+    if (nq == 0) return TM_OK;
+    const Tuning tu = tuning();
+    std::vector<QPlan> hp((size_t)nq);
+    std::vector<int> qstat((size_t)nq, TM_OK);
+    int first_err = TM_OK;
+    int64_t NW = 0;
+    int lmax = 1;
+    size_t wtab_bytes = 0;
+    for (int i = 0; i < nq; i++) {
+        std::string why;
+        int s = validate_query(g, qs[i], why);
+        if (s != TM_OK) {
+            qstat[(size_t)i] = s;
+            if (first_err == TM_OK) { first_err = s; set_error("query " + std::to_string(i) + ": " + why); }
+            std::memset(&hp[(size_t)i], 0, sizeof(QPlan));
+            hp[(size_t)i].l = 0;
+            hp[(size_t)i].J = 0;
+            hp[(size_t)i].win_base = NW;
+            continue;
+        }
+        fill_plan(hp[(size_t)i], qs[i], g);
+        hp[(size_t)i].win_base = NW;
+        NW += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].J * hp[(size_t)i].b;
+        lmax = std::max(lmax, hp[(size_t)i].l);
+        if (hp[(size_t)i].mode == TM_MODE_ESTIMATE && hp[(size_t)i].delta + 1 <= kWtabMax)
+            wtab_bytes += a256(16 * (size_t)(hp[(size_t)i].delta + 1));
+    }
+    // ---- scratch layout
+    size_t NWs = (size_t)std::max<int64_t>(NW, 1);
+    size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
+                7 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256;
+    char* sb = nullptr;
+    TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
+    char* p = sb;
+    auto take = [&](size_t bytes) { char* r = p; p += a256(bytes); return (void*)r; };
+    QPlan* dplans = (QPlan*)take(sizeof(QPlan) * (size_t)nq);
+    tm_result* dres = (tm_result*)take(sizeof(tm_result) * (size_t)nq);
+    for (int i = 0; i < nq; i++) {
+        QPlan& P = hp[(size_t)i];
+        if (P.l > 0 && P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) {
+            P.wtab = (const uint64_t*)take(16 * (size_t)(P.delta + 1));
+        }
+    }
+    WinDev W;
+    W.lo = (int64_t*)take(8 * NWs);
+    W.hi = (int64_t*)take(8 * NWs);
+    W.tend = (int64_t*)take(8 * NWs);
+    W.start = (int64_t*)take(8 * NWs);
+    W.j = (int64_t*)take(8 * NWs);
+    W.nfirst = (int64_t*)take(8 * NWs);
+    W.fbase = (int64_t*)take(8 * NWs);
+    W.q = (int32_t*)take(4 * NWs);
+    W.k = (int32_t*)take(4 * NWs);
+    W.kept = (int32_t*)take(4 * NWs);
+    W.qj = (double*)take(8 * NWs);
+    W.acc = (unsigned long long*)take(8 * A_N * NWs);
+    int64_t* dF = (int64_t*)take(8);
+    int64_t* dW2 = (int64_t*)take(8);
+    unsigned long long* dctr = (unsigned long long*)take(8);
+
+    int rc = TM_OK;
+    auto fail = [&](cudaError_t e, const char* what) {
+        if (rc == TM_OK && e != cudaSuccess) rc = cuda_status(e, what, __FILE__, __LINE__);
+    };
+    PhaseEvents pe(profiling());
+    auto wall0 = std::chrono::steady_clock::now();
+    int ev_w0 = pe.mark(st), ev_w1 = -1, ev_l0 = -1, ev_l1 = -1, ev_m1 = -1, ev_f1 = -1;
+    int64_t hW2 = 0;
+    fail(cudaMemcpyAsync(dplans, hp.data(), sizeof(QPlan) * (size_t)nq, cudaMemcpyHostToDevice, st), "plans");
+    fail(cudaMemsetAsync(W.acc, 0, 8 * A_N * NWs, st), "acc");
+    fail(cudaMemsetAsync(dctr, 0, 8, st), "counter");
+    for (int i = 0; i < nq && rc == TM_OK; i++) {
+        const QPlan& P = hp[(size_t)i];
+        if (P.wtab) {
+            int64_t n = P.delta + 1;
+            unsigned gr = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+            k_wtab<<<gr, 256, 0, st>>>((uint64_t*)P.wtab, P.delta, P.cd); count_launch();
+            fail(cudaGetLastError(), "k_wtab");
+        }
+    }
+    GraphDev G = g->dev;
+    int nsm = sm_count();
+    if (rc == TM_OK && NW > 0) {
+        unsigned gr = (unsigned)std::min<int64_t>((NW + 255) / 256, (int64_t)nsm * 16);
+        k_windows<<<gr, 256, 0, st>>>(G, dplans, nq, W, NW); count_launch();
+        fail(cudaGetLastError(), "k_windows");
+    }
+    if (rc == TM_OK) rc = scan_exclusive_i64(W.nfirst, W.fbase, NW, dF, st);
+    int64_t F = 0;
+    ev_w1 = pe.mark(st);
+    if (rc == TM_OK) {
+        fail(cudaMemcpyAsync(&F, dF, 8, cudaMemcpyDeviceToHost, st), "F readback");
+        fail(cudaStreamSynchronize(st), "sync F");
+    }
+    char* fb = nullptr;
+    if (rc == TM_OK && F > 0) {
+        size_t Fs = (size_t)F;
+        fail(cudaMallocAsync((void**)&fb, a256(4 * Fs) + 3 * a256(8 * Fs), st), "per-edge scratch");
+        if (rc == TM_OK) {
+            char* q2 = fb;
+            auto take2 = [&](size_t bytes) { char* r = q2; q2 += a256(bytes); return (void*)r; };
+            int32_t* fwin = (int32_t*)take2(4 * Fs);
+            int64_t* len2 = (int64_t*)take2(8 * Fs);
+            int64_t* lo2 = (int64_t*)take2(8 * Fs);
+            int64_t* excl = (int64_t*)take2(8 * Fs);
+            MatchArgs A;
+            A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = F;
+            A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
+            A.enum_threshold = tu.enum_threshold;
+            int bt = tu.block_threads;
+            int64_t gl2 = std::min<int64_t>((F + bt - 1) / bt, (int64_t)nsm * 8);
+            ev_l0 = pe.mark(st);
+            k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, len2, lo2); count_launch();
+            fail(cudaGetLastError(), "k_level2");
+            if (rc == TM_OK) rc = scan_exclusive_i64(len2, excl, F, dW2, st);
+            ev_l1 = pe.mark(st);
+            if (rc == TM_OK) {
+                int bps = tu.blocks_per_sm;
+                A.chunk = tu.chunk_items;
+                unsigned gm = (unsigned)(nsm * bps);
+                if (lmax <= 4) k_match<4><<<gm, bt, 0, st>>>(A);
+                else k_match<TM_L_MAX><<<gm, bt, 0, st>>>(A);
+                count_launch();
+                fail(cudaGetLastError(), "k_match");
+                ev_m1 = pe.mark(st);
+                if (pe.on) fail(cudaMemcpyAsync(&hW2, dW2, 8, cudaMemcpyDeviceToHost, st), "W2");
+            }
+        }
+    }
+    if (rc == TM_OK) {
+        int ev_f0 = pe.mark(st);
+        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres); count_launch();
+        fail(cudaGetLastError(), "k_fold");
+        ev_f1 = pe.mark(st);
+        if (ev_m1 < 0) ev_m1 = ev_f0;
+    }
+    if (rc == TM_OK) fail(cudaMemcpyAsync(res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
+    // optional window readback for one query
+    std::vector<int64_t> h_lo, h_hi, h_start, h_j;
+    std::vector<int32_t> h_k, h_kept;
+    std::vector<double> h_qj;
+    std::vector<unsigned long long> h_acc;
+    int64_t dq_base = 0, dq_n = 0;
+    if (rc == TM_OK && dbg && dbg->query >= 0 && dbg->query < nq && hp[(size_t)dbg->query].l > 0) {
+        const QPlan& P = hp[(size_t)dbg->query];
+        dq_n = P.mode == TM_MODE_EXACT ? 1 : P.J;
+        dq_base = P.win_base + (P.mode == TM_MODE_EXACT ? 0 : (int64_t)dbg->k * P.J);
+        if (dbg->k < 0 || dbg->k >= P.b) dq_n = 0;
+        size_t n = (size_t)dq_n;
+        h_lo.resize(n); h_hi.resize(n); h_start.resize(n); h_j.resize(n);
+        h_k.resize(n); h_kept.resize(n); h_qj.resize(n); h_acc.resize(n * A_N);
+        if (n) {
+            fail(cudaMemcpyAsync(h_lo.data(), W.lo + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_hi.data(), W.hi + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_start.data(), W.start + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_j.data(), W.j + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_k.data(), W.k + dq_base, 4 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_kept.data(), W.kept + dq_base, 4 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_qj.data(), W.qj + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_acc.data(), W.acc + dq_base * A_N, 8 * A_N * n, cudaMemcpyDeviceToHost, st), "dbg");
+        }
+    }
+    cudaError_t se = cudaStreamSynchronize(st);
+    fail(se, "batch sync");
+    if (pe.on && rc == TM_OK) {
+        double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+        store_profile_batch(pe.ms(ev_w0, ev_w1), pe.ms(ev_l0, ev_l1), ev_l1 >= 0 ? pe.ms(ev_l1, ev_m1) : 0.0,
+                            pe.ms(ev_m1 >= 0 && ev_l1 >= 0 ? ev_m1 : ev_f1, ev_f1), wall, hW2, F);
+    }
+    if (fb) cudaFreeAsync(fb, st);
+    cudaFreeAsync(sb, st);
+    if (rc != TM_OK) return rc;
+    if (dbg && dq_n > 0) {
+        const QPlan& P = hp[(size_t)dbg->query];
+        int64_t n_out = 0;
+        for (int64_t i = 0; i < dq_n; i++) {
+            if (!dbg->all_windows && !h_kept[(size_t)i]) continue;
+            if (n_out < dbg->cap && dbg->recs) {
+                tm_window_rec& r = dbg->recs[n_out];
+                r.k = h_k[(size_t)i];
+                r.kept = h_kept[(size_t)i];
+                r.j = h_j[(size_t)i];
+                r.start = h_start[(size_t)i];
+                r.lo = h_lo[(size_t)i];
+                r.hi = h_hi[(size_t)i];
+                r.count = (int64_t)h_acc[(size_t)i * A_N + A_COUNT];
+                r.w_int = h_acc[(size_t)i * A_N + A_WHI];
+                r.w_frac = h_acc[(size_t)i * A_N + A_WLO];
+                r.q = h_qj[(size_t)i];
+            }
+            n_out++;
+        }
+        dbg->n_out = n_out;
+        dbg->shift = P.mode == TM_MODE_EXACT ? 0 : -(int64_t)(draw(P.seed, (uint64_t)dbg->k, 0) % (uint64_t)P.cd);
+    }
+    for (int i = 0; i < nq; i++) {
+        if (qstat[(size_t)i] != TM_OK) {
+            std::memset(&res[i], 0, sizeof(tm_result));
+            res[i].status = qstat[(size_t)i];
+        } else if (res[i].status != TM_OK && first_err == TM_OK) {
+            first_err = res[i].status;
+            set_error("query " + std::to_string(i) + ": count or weight sum overflowed 2^63");
+        }
+    }
+    return first_err;
+}
+
+int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* count) {
+    if (!g || !m || !count) { set_error("NULL argument"); return TM_EINVAL; }
+    if (delta < 0 || delta >= ((int64_t)1 << 61)) { set_error("delta outside [0, 2^61)"); return TM_EINVAL; }
+    tm_query q;
+    std::memset(&q, 0, sizeof(q));
+    q.motif = m;
+    q.delta = delta;
+    q.mode = TM_MODE_EXACT;
+    QPlan P;
+    fill_plan(P, q, g);
+    cudaStream_t st;
+    TM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    char* sb = nullptr;
+    int rc = TM_OK;
+    cudaError_t e = cudaMallocAsync((void**)&sb, 512, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sb, &P, sizeof(P), cudaMemcpyHostToDevice, st);
+    unsigned long long* dc = (unsigned long long*)(sb + 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, 8, st);
+    if (e == cudaSuccess && g->m > 0) {
+        int nsm = sm_count();
+        unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, (int64_t)nsm * 8));
+        k_plain<<<gr, 256, 0, st>>>(g->dev, (const QPlan*)sb, dc); count_launch();
+        e = cudaGetLastError();
+    }
+    unsigned long long hc = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, dc, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_status(e, "tm_count_exact_plain", __FILE__, __LINE__);
+    if (sb) cudaFreeAsync(sb, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc == TM_OK) {
+        if (hc >= (1ull << 63)) { set_error("count overflowed 2^63"); return TM_EOVERFLOW; }
+        *count = (int64_t)hc;
+    }
+    return rc;
+}
+
+}  // namespace tmo

@@ -1,0 +1,276 @@
+// Device primitives: exclusive scan of int64 and a stable LSD radix sort of
+// (uint32 key, uint32 value) pairs.  Neither waits on other blocks: the scan
+// is reduce-then-scan over tiles, the sort is histogram / scan / scatter per
+// digit, so no launch can spin.
+#include <vector>
+
+#include "tm_internal.cuh"
+
+namespace tmo {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;   // 2048
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the block total in *total
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* smem, int64_t* total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t inc = warp_incl_scan(v);
+    if (lane == 31) smem[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int64_t s = lane < nw ? smem[lane] : 0;
+        int64_t si = warp_incl_scan(s);
+        if (lane < nw) smem[lane] = si - s;
+        if (lane == nw - 1) smem[32] = si;
+    }
+    __syncthreads();
+    int64_t r = inc - v + smem[w];
+    *total = smem[32];
+    __syncthreads();
+    return r;
+}
+
+// Each block scans one tile (exclusive), writes the tile total to sums[tile].
+__global__ void k_scan_tiles(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                             int64_t* __restrict__ sums) {
+    __shared__ int64_t smem[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        loc += v[i];
+    }
+    int64_t total;
+    int64_t run = block_excl_scan(loc, smem, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ offs) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t add = offs[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] += add;
+    }
+}
+
+__global__ void k_scan_small(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                             int64_t* __restrict__ d_total) {
+    // single block, n <= kScanTile
+    __shared__ int64_t smem[33];
+    int64_t base = (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        loc += v[i];
+    }
+    int64_t total;
+    int64_t run = block_excl_scan(loc, smem, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = total;
+}
+
+__global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
+
+// ------------------------------------------------------------------ radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;                       // per lane
+constexpr int kSortTile = kSortThreads * kSortItems; // 4096
+constexpr int kMaxDigitBits = 8;
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int db,
+                             int32_t* __restrict__ hist, int64_t ntiles) {
+    __shared__ int32_t h[1 << kMaxDigitBits];
+    int nd = 1 << db;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    uint32_t mask = (uint32_t)nd - 1;
+    for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
+        int64_t idx = base + i;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & mask], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) hist[(int64_t)i * ntiles + blockIdx.x] = h[i];
+}
+
+__global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+// Stable scatter of one tile: warp w owns items [w*512, w*512+512) of the
+// tile, taken 32 at a time in index order; ranks among equal digits come from
+// __match_any_sync and per-warp running counters, then warps are offset by
+// the counts of lower warps.
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+                int db, const int64_t* __restrict__ offs, int64_t ntiles) {
+    __shared__ int32_t cnt[kSortWarps][1 << kMaxDigitBits];
+    int nd = 1 << db;
+    uint32_t mask = (uint32_t)nd - 1;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = lane; i < nd; i += 32) cnt[w][i] = 0;
+    __syncwarp();
+    int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * (kSortItems * 32);
+    uint32_t key[kSortItems], val[kSortItems];
+    int32_t rank[kSortItems];
+    unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        int64_t idx = base + r * 32 + lane;
+        bool ok = idx < n;
+        key[r] = ok ? kin[idx] : 0u;
+        val[r] = ok ? vin[idx] : 0u;
+        uint32_t d = ok ? ((key[r] >> shift) & mask) : 0xffffffffu;
+        unsigned peers = __match_any_sync(kFull, d);
+        int before = __popc(peers & lt);
+        int32_t c0 = ok ? cnt[w][d] : 0;
+        rank[r] = c0 + before;
+        __syncwarp();
+        int leader = 31 - __clz(peers);
+        if (ok && lane == leader) cnt[w][d] = c0 + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        int32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ww++) {
+            int32_t c = cnt[ww][d];
+            cnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        int64_t idx = base + r * 32 + lane;
+        if (idx < n) {
+            uint32_t d = (key[r] >> shift) & mask;
+            int64_t pos = offs[(int64_t)d * ntiles + blockIdx.x] + cnt[w][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+}  // namespace
+
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,
+                       cudaStream_t st) {
+    if (n <= 0) {
+        if (d_total) {
+            k_set_i64<<<1, 1, 0, st>>>(d_total, 0); count_launch();
+            TM_CUDA(cudaGetLastError());
+        }
+        return TM_OK;
+    }
+    if (n <= kScanTile) {
+        k_scan_small<<<1, kScanThreads, 0, st>>>(in, out, n, d_total); count_launch();
+        TM_CUDA(cudaGetLastError());
+        return TM_OK;
+    }
+    int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    int64_t* sums = nullptr;
+    TM_CUDA(cudaMallocAsync((void**)&sums, sizeof(int64_t) * (size_t)ntiles * 2, st));
+    int64_t* soffs = sums + ntiles;
+    k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, n, sums); count_launch();
+    int s1 = cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;
+    if (s1 == TM_OK) s1 = scan_exclusive_i64(sums, soffs, ntiles, d_total, st);
+    if (s1 == TM_OK) {
+        k_scan_add<<<(unsigned)ntiles, kScanThreads, 0, st>>>(out, n, soffs); count_launch();
+        if (cudaGetLastError() != cudaSuccess) s1 = TM_ECUDA;
+    }
+    cudaFreeAsync(sums, st);
+    if (s1 != TM_OK) set_error("scan launch failed");
+    return s1;
+}
+
+int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                     int64_t n, int bits, cudaStream_t st) {
+    // Sorts (keys, vals) stably by the low `bits` bits of keys; the result ends
+    // in keys/vals.  bits <= 32.
+    if (n <= 1 || bits <= 0) return TM_OK;
+    int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    int db = (bits + passes - 1) / passes;
+    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    int64_t nh = ((int64_t)1 << db) * ntiles;
+    int32_t* hist = nullptr;
+    int64_t* offs = nullptr;
+    TM_CUDA(cudaMallocAsync((void**)&hist, sizeof(int32_t) * (size_t)nh, st));
+    TM_CUDA(cudaMallocAsync((void**)&offs, sizeof(int64_t) * (size_t)nh * 2, st));
+    int64_t* hist64 = offs + nh;
+    uint32_t *ka = keys, *va = vals, *kb = keys_tmp, *vb = vals_tmp;
+    int rc = TM_OK;
+    for (int p = 0; p < passes && rc == TM_OK; p++) {
+        int shift = p * db;
+        int width = (shift + db > bits) ? bits - shift : db;
+        k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ka, n, shift, width, hist, ntiles); count_launch();
+        int64_t nhp = ((int64_t)1 << width) * ntiles;
+        k_i32_to_i64<<<(unsigned)((nhp + 255) / 256 < 4096 ? (nhp + 255) / 256 : 4096), 256, 0, st>>>(hist, hist64, nhp); count_launch();
+        rc = scan_exclusive_i64(hist64, offs, nhp, nullptr, st);
+        if (rc != TM_OK) break;
+        k_radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, width,
+                                                                  offs, ntiles); count_launch();
+        if (cudaGetLastError() != cudaSuccess) { rc = TM_ECUDA; break; }
+        uint32_t* t;
+        t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    if (rc == TM_OK && ka != keys) {
+        cudaMemcpyAsync(keys, ka, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(vals, va, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(offs, st);
+    if (rc != TM_OK) set_error("radix sort launch failed");
+    return rc;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace tmo

@@ -1,0 +1,222 @@
+// Internal declarations of libtmotif (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tm.h"
+
+namespace tmo {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ----------------------------------------------------------------------------
+// error plumbing
+// ----------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define TM_CUDA(call)                                                             \
+    do {                                                                          \
+        cudaError_t _e = (call);                                                  \
+        if (_e != cudaSuccess) return ::tmo::cuda_status(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define TM_TRY(call)                   \
+    do {                               \
+        int _s = (call);               \
+        if (_s != TM_OK) return _s;    \
+    } while (0)
+
+// ----------------------------------------------------------------------------
+// device graph: edges sorted by time plus three time-sorted adjacency views
+// ----------------------------------------------------------------------------
+struct GraphDev {
+    int64_t m;
+    int32_t n;
+    int64_t P;              // distinct (src, dst) pairs
+    const int32_t* src;     // [m]
+    const int32_t* dst;     // [m]
+    const int64_t* t;       // [m] normalised, non-decreasing
+    const int64_t* out_off; // [n+1]
+    const int32_t* out_nbr; // [m] destination
+    const int64_t* out_t;   // [m]
+    const int64_t* in_off;  // [n+1]
+    const int32_t* in_nbr;  // [m] source
+    const int64_t* in_t;    // [m]
+    const int64_t* pk_off;  // [n+1] pair index range of each source
+    const int32_t* pair_dst;// [P]
+    const int64_t* pair_off;// [P+1]
+    const int64_t* pair_t;  // [m]
+};
+
+}  // namespace tmo
+
+struct tm_graph {
+    int device;
+    int64_t m;
+    int32_t n;
+    int64_t P;
+    int64_t t_min;
+    int64_t t_max;          // normalised
+    int64_t bytes;
+    void* block;            // one device allocation holding every array
+    tmo::GraphDev dev;
+};
+
+namespace tmo {
+
+// ----------------------------------------------------------------------------
+// motif plans
+// ----------------------------------------------------------------------------
+enum View : int8_t { kPair = 0, kOut = 1, kIn = 2, kAll = 3 };
+
+struct LevelPlan {
+    int8_t view;    // which adjacency view lists the candidates of this motif edge
+    int8_t su, sv;  // motif node labels of u_i, v_i
+    int8_t bind_u;  // u_i is first seen at this edge
+    int8_t bind_v;  // v_i is first seen at this edge
+    int8_t nb;      // labels 0..nb-1 are bound before this edge
+    int8_t pad[2];
+};
+
+}  // namespace tmo
+
+struct tm_motif {
+    int32_t l, k;
+    int32_t mu[TM_L_MAX];
+    int32_t mv[TM_L_MAX];
+    tmo::LevelPlan lv[TM_L_MAX];
+};
+
+namespace tmo {
+
+struct QPlan {
+    int32_t l, k;
+    int32_t mode;        // TM_MODE_*
+    int32_t b;
+    int32_t q_mode;
+    int32_t pad0;
+    int64_t delta;
+    int64_t cd;          // c * delta (estimate), 0 for exact
+    int64_t J;           // windows per shift (estimate), 1 for exact
+    int64_t win_base;    // first window slot of this query
+    double p;
+    uint64_t seed;
+    const uint64_t* wtab;// [2*(delta+1)] Q64 weights c delta / (c delta - Delta), or null
+    LevelPlan lv[TM_L_MAX];
+};
+
+struct Tuning {
+    int block_threads = 256;
+    int blocks_per_sm = 4;
+    int chunk_items = 256;
+    int enum_threshold = 48;
+};
+Tuning& tuning();
+
+struct BatchOut {                 // optional per-window readback for one query
+    int query = -1;
+    int32_t k = 0;
+    bool all_windows = false;
+    tm_window_rec* recs = nullptr;
+    int64_t cap = 0;
+    int64_t n_out = 0;
+    int64_t shift = 0;
+};
+
+int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res,
+              cudaStream_t st, BatchOut* dbg);
+int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* count);
+
+// primitives (prims.cu)
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,
+                       cudaStream_t st);
+int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                     int64_t n, int bits, cudaStream_t st);
+
+int sm_count();
+
+// profiling (abi.cu): phase events of the last batch / graph build, launch counter
+bool profiling();
+void store_profile_batch(double windows_ms, double level2_ms, double match_ms, double fold_ms,
+                         double batch_ms, int64_t match_items, int64_t first_edges);
+void store_profile_graph(double graph_ms);
+void count_launch(int n = 1);
+
+// CUDA events on a stream, created only while profiling is on
+struct PhaseEvents {
+    cudaEvent_t ev[8];
+    int n = 0;
+    bool on = false;
+    explicit PhaseEvents(bool enable) : on(enable) {
+        if (on)
+            for (int i = 0; i < 8; i++)
+                if (cudaEventCreate(&ev[i]) != cudaSuccess) on = false;
+    }
+    ~PhaseEvents() {
+        if (on)
+            for (int i = 0; i < 8; i++) cudaEventDestroy(ev[i]);
+    }
+    int mark(cudaStream_t st) {
+        if (!on || n >= 8) return -1;
+        cudaEventRecord(ev[n], st);
+        return n++;
+    }
+    double ms(int a, int b) const {
+        if (!on || a < 0 || b < 0) return 0.0;
+        float x = 0.f;
+        cudaEventElapsedTime(&x, ev[a], ev[b]);
+        return (double)x;
+    }
+};
+
+// ----------------------------------------------------------------------------
+// device helpers
+// ----------------------------------------------------------------------------
+// first index p in [lo, hi) with a[p] > v (a sorted non-decreasingly)
+__device__ __forceinline__ int64_t upper_bound_i64(const int64_t* __restrict__ a, int64_t lo,
+                                                   int64_t hi, int64_t v) {
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(a + mid) <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+// first index p in [lo, hi) with a[p] >= v
+__device__ __forceinline__ int64_t lower_bound_i64(const int64_t* __restrict__ a, int64_t lo,
+                                                   int64_t hi, int64_t v) {
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(a + mid) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo,
+                                                   int64_t hi, int32_t v) {
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(a + mid) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): output n (n >= 1) of the generator
+// seeded with s is mix(s + n * 0x9E3779B97F4A7C15).
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_output(uint64_t seed, uint64_t n) {
+    return sm64_mix(seed + n * 0x9E3779B97F4A7C15ull);
+}
+// draw n of repetition k of a query seeded with `seed`
+__host__ __device__ __forceinline__ uint64_t draw(uint64_t seed, uint64_t k, uint64_t n) {
+    return sm64_output(sm64_output(seed, k + 1), n + 1);
+}
+
+}  // namespace tmo

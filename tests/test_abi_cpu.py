@@ -1,0 +1,96 @@
+"""CPU checks of the C ABI: the CUDA library builds for sm_103a, loads without
+a GPU, exports every function include/tm.h declares, and the binding's
+structs have the C layout.  No compute calls."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tm.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1810_00980_gb300 import tm
+    return tm
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("tm_graph_load", "tm_motif_compile", "tm_count_exact", "tm_estimate",
+                     "tm_estimate_windows", "tm_run_batch", "tm_serve_submit", "tm_serve_poll"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    L = built.lib()
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding covers them all
+    assert set(_declared_functions()) <= set(built._SIGS)
+
+
+def test_nm_shows_exports(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (tm_\w+)", out))
+    assert set(_declared_functions()) <= exported
+
+
+def test_struct_layouts_match_c(built, tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tm.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                    'sizeof(tm_graph_info), sizeof(tm_window_rec), sizeof(tm_query), sizeof(tm_result),'
+                    'sizeof(tm_tuning), sizeof(tm_serve_cfg), offsetof(tm_result, var_hat),'
+                    'offsetof(tm_profile, launches),'
+                    'offsetof(tm_query, q_mode));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    vals = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    import ctypes
+    tm = built
+    assert vals == [ctypes.sizeof(tm.GraphInfo), ctypes.sizeof(tm.WindowRec), ctypes.sizeof(tm.QueryC),
+                    ctypes.sizeof(tm.ResultC), ctypes.sizeof(tm.TuningC), ctypes.sizeof(tm.ServeCfg),
+                    tm.ResultC.var_hat.offset, tm.ProfileC.launches.offset, tm.QueryC.q_mode.offset]
+
+
+def test_strerror_without_gpu(built):
+    L = built.lib()
+    assert L.tm_strerror(0) == b"ok"
+    assert L.tm_strerror(built.TM_EUNSORTED) == b"timestamps not sorted"
+    assert L.tm_version().startswith(b"libtmotif")
+
+
+def test_motif_compile_rejects_bad_motifs(built):
+    """Host-only validation (Def. 2.1: motif edges join two distinct nodes)."""
+    tm = built
+    with pytest.raises(tm.TmError) as e:
+        tm.Motif([0, 1], [1, 1])
+    assert e.value.status == tm.TM_EINVAL
+    with pytest.raises(tm.TmError):
+        tm.Motif([], [])
+    with pytest.raises(tm.TmError):
+        tm.Motif(list(range(9)), list(range(1, 10)))   # l > TM_L_MAX
+    m = tm.Motif([5, 7, 9], [7, 9, 5])
+    assert m.l == 3
+
+
+def test_product_has_no_oracle_dependency():
+    """The library package never imports, links or runs the oracle."""
+    pkg = os.path.join(ROOT, "paper_1810_00980_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.lower() or f == "synth.py", f

@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Counts are compared bit-exactly as int64; estimates within 1e-12 relative
+(the weights are exact Q64 integer sums on the device and exactly rounded
+rationals in the oracle, so both sit within a few fp64 ulps of the true
+value).  Per-window weights W_j are compared against the oracle's correctly
+rounded value with the same 1e-12 relative bound plus the device's documented
+floor error of at most 2^-64 per instance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1810_00980_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+EST_RTOL = 1e-12
+
+MOTIFS = [
+    ([0], [1]),
+    ([0, 1], [1, 0]),
+    ([0, 0], [1, 1]),
+    ([0, 1], [1, 2]),
+    ([1, 0], [0, 2]),
+    ([0, 2], [1, 1]),
+    ([0, 1, 2], [1, 2, 0]),
+    ([2, 2, 2], [0, 1, 0]),
+    ([0, 1, 0], [1, 0, 1]),
+    ([0, 2, 1], [1, 3, 2]),
+    ([0, 1, 2, 3], [1, 2, 3, 0]),
+    ([0, 0, 0, 0], [1, 2, 1, 2]),
+    ([1, 0, 2, 0], [0, 2, 1, 1]),
+    ([0, 1, 2, 3, 4], [1, 2, 3, 4, 0]),
+    ([0, 1, 0, 1, 0, 1], [1, 0, 1, 0, 1, 0]),
+    ([0, 1, 2, 3, 4, 5, 6, 0], [1, 2, 3, 4, 5, 6, 7, 7]),
+]
+
+
+@pytest.fixture(scope="module")
+def tm():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    from paper_1810_00980_gb300 import tm as _tm
+    return _tm
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.core.build()
+    return oracle
+
+
+def _graph(tm, src, dst, t, device=True, n_nodes=-1):
+    import torch
+    if device and len(t):
+        return tm.Graph(torch.from_numpy(np.ascontiguousarray(src)).cuda(),
+                        torch.from_numpy(np.ascontiguousarray(dst)).cuda(),
+                        torch.from_numpy(np.ascontiguousarray(t)).cuda(), n_nodes)
+    return tm.Graph(src, dst, t, n_nodes)
+
+
+def _close(a, b, rtol=EST_RTOL):
+    return abs(a - b) <= rtol * max(abs(b), 1e-300) or (a == 0 and b == 0)
+
+
+# ------------------------------------------------------------------ exact ---
+def test_exact_random_tiny_graphs(tm, orc):
+    """Many tiny graphs with ties, duplicates and self-loops, every motif shape."""
+    rng = np.random.default_rng(2024)
+    for trial in range(60):
+        n = int(rng.integers(2, 7))
+        m = int(rng.integers(0, 60))
+        src, dst, t = synth.random_small_graph(rng, n, m, int(rng.integers(1, 80)), self_loops=trial % 4 == 0)
+        g = _graph(tm, src, dst, t, device=trial % 2 == 0)
+        for ms, md in MOTIFS:
+            mo = tm.Motif(ms, md)
+            for delta in (0, 3, 17, 1000):
+                want = orc.count_exact(src, dst, t, ms, md, delta)
+                assert tm.count_exact(g, mo, delta) == want, (trial, ms, md, delta)
+                if trial % 5 == 0:
+                    assert tm.count_exact_plain(g, mo, delta) == want
+
+
+def test_exact_bruteforce_small(tm, orc):
+    """Def. 2.2 by exhaustive subsets on <= 12 edges, directly against the device."""
+    rng = np.random.default_rng(12)
+    for trial in range(40):
+        src, dst, t = synth.random_small_graph(rng, 4, int(rng.integers(0, 13)), 15, self_loops=trial % 3 == 0)
+        g = _graph(tm, src, dst, t)
+        for ms, md in MOTIFS[:13]:
+            want, _ = orc.count_bruteforce(src, dst, t, ms, md, 9)
+            assert tm.count_exact(g, tm.Motif(ms, md), 9) == want
+
+
+def test_exact_mid_graph_all_config_motifs(tm, orc):
+    """A bursty power-law graph spanning many matcher chunks and ragged tails."""
+    src, dst, t = synth.chung_lu_hawkes(3000, 300_000, 2.1, seed=21, horizon=6_000_000)
+    g = _graph(tm, src, dst, t)
+    for name in ("cycle3", "outstar3", "pingpong", "cycle4"):
+        ms, md = synth.MOTIFS[name]
+        mo = tm.Motif(ms, md)
+        for delta in (600, 3600, 86400):
+            want = orc.count_exact(src, dst, t, ms, md, delta, threads=8)
+            got = tm.count_exact(g, mo, delta)
+            assert got == want, (name, delta, got, want)
+
+
+def test_hub_heavy_graph(tm, orc):
+    """Hub bursts: thousands of edges from one node inside one delta."""
+    src, dst, t = synth.chung_lu_hawkes(2000, 120_000, 1.8, seed=5, horizon=3_000_000,
+                                        max_degree=40_000, hub_bursts=6, burst_max=4000)
+    g = _graph(tm, src, dst, t)
+    for name in ("outstar3", "cycle3", "cycle4"):
+        ms, md = synth.MOTIFS[name]
+        mo = tm.Motif(ms, md)
+        want = orc.count_exact(src, dst, t, ms, md, 1800, threads=8)
+        assert tm.count_exact(g, mo, 1800) == want
+    # the subtraction path of the last level (one endpoint new, long ranges)
+    for thr in (1, 1 << 20):
+        tm.set_tuning(enum_threshold=thr)
+        for ms, md in (([0, 0], [1, 2]), ([1, 2], [0, 0]), ([0, 1, 1], [1, 2, 3])):
+            want = orc.count_exact(src, dst, t, ms, md, 600, threads=8)
+            assert tm.count_exact(g, tm.Motif(ms, md), 600) == want
+    tm.set_tuning(enum_threshold=48)
+
+
+def test_edge_cases(tm, orc):
+    tmm = tm
+    cyc = tmm.Motif([0, 1, 2], [1, 2, 0])
+    # empty graph
+    e32 = np.zeros(0, np.int32)
+    g = tmm.Graph(e32, e32, np.zeros(0, np.int64), 5)
+    assert tmm.count_exact(g, cyc, 10) == 0
+    assert tmm.estimate(g, cyc, 10, 3, 0.5, 1) == 0.0
+    # one edge, l = 1
+    g = _graph(tm, np.array([0], np.int32), np.array([1], np.int32), np.array([7], np.int64))
+    assert tmm.count_exact(g, tmm.Motif([0], [1]), 0) == 1
+    # all timestamps equal: nothing with l >= 2
+    s = np.array([0, 1, 2, 0, 1], np.int32)
+    d = np.array([1, 2, 0, 2, 0], np.int32)
+    t = np.full(5, 42, np.int64)
+    g = _graph(tm, s, d, t)
+    assert tmm.count_exact(g, cyc, 100) == 0
+    assert tmm.count_exact(g, tmm.Motif([0], [1]), 0) == 5
+    # unsorted and out-of-range inputs are rejected on the host
+    with pytest.raises(tmm.TmError) as ei:
+        tmm.Graph(np.array([0, 1], np.int32), np.array([1, 0], np.int32), np.array([5, 4], np.int64))
+    assert ei.value.status == tmm.TM_EUNSORTED
+    with pytest.raises(tmm.TmError) as ei:
+        tmm.Graph(np.array([0, 3], np.int32), np.array([1, 0], np.int32), np.array([4, 5], np.int64), 3)
+    assert ei.value.status == tmm.TM_ERANGE
+    with pytest.raises(tmm.TmError) as ei:
+        tmm.Graph(np.array([0, -1], np.int32), np.array([1, 0], np.int32), np.array([4, 5], np.int64))
+    assert ei.value.status == tmm.TM_ERANGE
+    # bad query arguments
+    g = _graph(tm, s, d, np.arange(5, dtype=np.int64))
+    for args in ((10, 0, 0.5, 1), (10, 3, 0.0, 1), (10, 3, 1.5, 1), (0, 3, 0.5, 1)):
+        with pytest.raises(tmm.TmError) as ei:
+            tmm.estimate(g, cyc, *args)
+        assert ei.value.status == tmm.TM_EINVAL
+    with pytest.raises(tmm.TmError):
+        tmm.count_exact(g, cyc, -1)
+    # negative and huge timestamps: normalisation t - t_min
+    t2 = np.array([-(1 << 40), -(1 << 40) + 1, -(1 << 40) + 2], np.int64)
+    g = _graph(tm, np.array([0, 1, 2], np.int32), np.array([1, 2, 0], np.int32), t2)
+    assert tmm.count_exact(g, cyc, 2) == 1
+    assert g.info().t_min == -(1 << 40) and g.info().t_max == 2
+
+
+def test_device_and_host_load_agree(tm):
+    src, dst, t = synth.config1_graph()
+    a = _graph(tm, src, dst, t, device=True)
+    b = _graph(tm, src, dst, t, device=False)
+    ia, ib = a.info(), b.info()
+    assert (ia.m, ia.n_nodes, ia.n_pairs, ia.t_max) == (ib.m, ib.n_nodes, ib.n_pairs, ib.t_max)
+    assert ia.n_pairs == len(set(zip(src.tolist(), dst.tolist())))
+    mo = tm.Motif([0, 1], [1, 0])
+    assert tm.count_exact(a, mo, 50_000) == tm.count_exact(b, mo, 50_000)
+
+
+# ---------------------------------------------------------------- estimate ---
+def _check_windows(tm, orc, g, src, dst, t, ms, md, delta, c, p, seed, k=0):
+    mo = tm.Motif(ms, md)
+    shift, recs = tm.estimate_windows(g, mo, delta, c, p, seed, k=k, all_windows=True)
+    s_or, rec_or = orc.window_records(src, dst, t, ms, md, delta, c, seed, k=k, p=p, only_kept=False,
+                                      threads=4)
+    assert shift == s_or
+    assert len(recs) == len(rec_or)
+    for a, b in zip(recs, rec_or):
+        assert (a["j"], a["start"], a["lo"], a["hi"], a["kept"]) == (b["j"], b["a"], b["lo"], b["hi"], b["kept"])
+        assert a["count"] == b["count"], (a, b)
+        w = a["w_int"] + a["w_frac"] * 2.0 ** -64
+        assert abs(w - b["W"]) <= EST_RTOL * b["W"] + b["count"] * 2.0 ** -64 + 1e-300
+    return recs
+
+
+def test_config1_exact_and_estimate(tm, orc):
+    """Config 1 in full: N=1,000, M=20,000 uniform; cycle, delta=3,600;
+    estimate with c=30, p=0.1, seed 1."""
+    src, dst, t = synth.config1_graph()
+    g = _graph(tm, src, dst, t)
+    ms, md = synth.MOTIFS["cycle3"]
+    mo = tm.Motif(ms, md)
+    assert tm.count_exact(g, mo, 3600) == orc.count_exact(src, dst, t, ms, md, 3600)
+    z = tm.estimate(g, mo, 3600, 30, 0.1, 1)
+    assert _close(z, orc.estimate(src, dst, t, ms, md, 3600, 30, 0.1, 1))
+    _check_windows(tm, orc, g, src, dst, t, ms, md, 3600, 30, 0.1, 1)
+    # wider spans so that windows hold instances
+    for delta in (20_000, 100_000):
+        assert tm.count_exact(g, mo, delta) == orc.count_exact(src, dst, t, ms, md, delta)
+        for (c, p, seed) in ((2, 0.5, 3), (3, 1.0, 4), (1, 0.7, 5)):
+            z = tm.estimate(g, mo, delta, c, p, seed)
+            zo = orc.estimate(src, dst, t, ms, md, delta, c, p, seed)
+            assert _close(z, zo), (delta, c, p, seed, z, zo)
+        _check_windows(tm, orc, g, src, dst, t, ms, md, delta, 2, 0.5, 3)
+
+
+def test_estimate_mid_graph_parity(tm, orc):
+    src, dst, t = synth.chung_lu_hawkes(3000, 300_000, 2.1, seed=22, horizon=6_000_000)
+    g = _graph(tm, src, dst, t)
+    for name in ("cycle3", "outstar3", "pingpong", "cycle4"):
+        ms, md = synth.MOTIFS[name]
+        mo = tm.Motif(ms, md)
+        for (delta, c, p, seed) in ((600, 10, 0.1, 1), (3600, 30, 0.3, 2), (3600, 2, 1.0, 3)):
+            z = tm.estimate(g, mo, delta, c, p, seed)
+            zo = orc.estimate(src, dst, t, ms, md, delta, c, p, seed, threads=8)
+            assert _close(z, zo), (name, delta, c, p, seed, z, zo)
+    _check_windows(tm, orc, g, src, dst, t, *synth.MOTIFS["outstar3"], 3600, 10, 0.2, 9, k=2)
+
+
+def test_batch_mixed_queries_match_single(tm, orc):
+    """One batched launch of exact and estimate queries (several motifs, deltas,
+    c, p, b and both q_j rules) gives each query's single-query answer and the
+    oracle's."""
+    src, dst, t = synth.chung_lu_hawkes(2000, 150_000, 2.1, seed=23, horizon=4_000_000)
+    g = _graph(tm, src, dst, t)
+    motifs = {n: tm.Motif(*synth.MOTIFS[n]) for n in ("cycle3", "outstar3", "pingpong", "cycle4")}
+    qs, want = [], []
+    for i, (n, mo) in enumerate(motifs.items()):
+        ms, md = synth.MOTIFS[n]
+        qs.append(tm.exact_query(mo, 3600))
+        want.append(("exact", orc.count_exact(src, dst, t, ms, md, 3600, threads=8)))
+        qs.append(tm.estimate_query(mo, 3600, 10, 0.25, 100 + i))
+        want.append(("est", orc.estimate(src, dst, t, ms, md, 3600, 10, 0.25, 100 + i, threads=8)))
+        qs.append(tm.estimate_query(mo, 600, 30, 0.5, 200 + i, b=3))
+        want.append(("est", orc.estimate(src, dst, t, ms, md, 600, 30, 0.5, 200 + i, b=3, threads=8)))
+        r = 20.0
+        qfun = lambda j, a, e, _t=t, _r=r: min(1.0, _r * float(np.sum((_t - _t.min() >= a) & (_t - _t.min() <= e))) / len(_t))
+        qs.append(tm.estimate_query(mo, 3600, 10, r, 300 + i, q_mode=tm.TM_Q_EDGES))
+        want.append(("est", orc.estimate(src, dst, t, ms, md, 3600, 10, None, 300 + i, q=qfun, threads=8)))
+    res = tm.run_batch(g, qs)
+    for q, r, (kind, w) in zip(qs, res, want):
+        assert r["status"] == 0
+        if kind == "exact":
+            assert r["count"] == w
+        else:
+            assert _close(r["estimate"], w), (r, w)
+    # alone == in the mix
+    for q, r in zip(qs, res):
+        alone = tm.run_batch(g, [q])[0]
+        assert alone["count"] == r["count"] and alone["estimate"] == r["estimate"]
+
+
+def test_variance_estimate_is_lemma44(tm, orc):
+    """var_hat = sum over kept windows of Y_j^2 (1 - p) / p^2, an unbiased
+    estimate of Var[Z | s] = sum_j Y_j^2 (1 - p)/p (Lemma 4.4)."""
+    src, dst, t = synth.chung_lu_hawkes(2000, 150_000, 2.1, seed=24, horizon=4_000_000)
+    g = _graph(tm, src, dst, t)
+    ms, md = synth.MOTIFS["outstar3"]
+    mo = tm.Motif(ms, md)
+    p = 0.3
+    r = tm.run_batch(g, [tm.estimate_query(mo, 3600, 10, p, 7)])[0]
+    s, recs = orc.window_records(src, dst, t, ms, md, 3600, 10, 7, p=p, threads=8)
+    want = math.fsum(x["W"] ** 2 * (1 - p) / p ** 2 for x in recs if x["kept"])
+    assert abs(r["var_hat"] - want) <= 1e-9 * want
+
+
+# --------------------------------------------------- full size, sampled -----
+@pytest.mark.slow
+def test_config2_full_size_sampled_windows(tm, orc):
+    """Config 2 size (N=1e5, M=1e7, Chung-Lu 2.1 + Hawkes): the batched path in
+    the benchmark's launch configuration; per-window exact counts and weights of
+    sampled kept windows checked one by one against the oracle, and one full
+    exact count."""
+    src, dst, t = synth.config2_graph()
+    g = _graph(tm, src, dst, t)
+    tn = t - t.min()
+    for name in ("cycle3", "outstar3", "pingpong"):
+        ms, md = synth.MOTIFS[name]
+        mo = tm.Motif(ms, md)
+        for delta in (600, 3600):
+            shift, recs = tm.estimate_windows(g, mo, delta, 30, 0.1, 11)
+            nz = [r for r in recs if r["hi"] > r["lo"]]
+            rng = np.random.default_rng(delta)
+            pick = rng.choice(len(nz), size=min(6, len(nz)), replace=False)
+            cd = 30 * delta
+            for i in pick:
+                r = nz[int(i)]
+                lo, hi = r["lo"], r["hi"]
+                assert np.all(tn[lo:hi] >= r["start"]) and np.all(tn[lo:hi] <= r["start"] + cd - 1)
+                cnt, hist, _ = orc.count_exact_hist(src[lo:hi], dst[lo:hi], tn[lo:hi], ms, md, delta,
+                                                    threads=8, n_nodes=100_000)
+                assert r["count"] == cnt
+                wo = math.fsum((int(hist[d]) * cd) / (cd - d) for d in np.nonzero(hist)[0])
+                w = r["w_int"] + r["w_frac"] * 2.0 ** -64
+                assert abs(w - wo) <= EST_RTOL * wo + cnt * 2.0 ** -64
+    ms, md = synth.MOTIFS["pingpong"]
+    want = orc.count_exact(src, dst, t, ms, md, 600, threads=16)
+    res = tm.run_batch(g, [tm.exact_query(tm.Motif(ms, md), 600)])[0]
+    assert res["count"] == want
