@@ -358,8 +358,14 @@ def main():
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "k_match_traffic.json")
     if os.path.exists(tfile):
+        # counters are only valid for the kernel source they were taken on
         try:
-            traffic = json.load(open(tfile)).get("traffic_bytes_per_launch")
+            import hashlib
+            tj = json.load(open(tfile))
+            src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_1810_00980_gb300", "csrc", "match.cu"),
+                                           "rb").read()).hexdigest()[:16]
+            if tj.get("source_sha256_16") == src_hash:
+                traffic = tj.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
 
