@@ -178,6 +178,35 @@ int tm_estimate_windows(const tm_graph* g, const tm_motif* m, int64_t delta, int
 int tm_run_batch(const tm_graph* g, const tm_query* queries, int32_t n_queries,
                  tm_result* results, void* stream);
 
+/* ---- exact count without allocation ------------------------------------------
+ * The paper has no counterpart to this call; it exists for deployments.
+ *
+ * tm_count_exact_noalloc returns the same C_M as tm_count_exact, for callers
+ * that may not allocate device memory while they answer queries: a process
+ * whose device memory is reserved up front by another allocator (for example
+ * a framework's caching allocator that owns the whole GPU, or a fixed memory
+ * budget), or latency-critical code that forbids allocation after start-up
+ * because cudaMalloc/cudaFree can block and synchronise the device.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine.  Its scratch is one
+ * static device array compiled into the library, TM_NOALLOC_SCRATCH_BYTES
+ * (about 7.4 MB) on every GPU that loads the library, held until the process
+ * exits.
+ *   g       graph with at most TM_NOALLOC_MAX_EDGES edges (else TM_EINVAL).
+ *   stream  cudaStream_t as void* (NULL: legacy default stream); the work is
+ *           ordered on it and the call returns once *count is on the host.
+ *   count   host pointer receiving C_M.
+ * The first call on a device resolves the array's device address with
+ * cudaGetSymbolAddress (which can load the library's device code); make that
+ * first call before any stream capture.  Every call uses the same array and
+ * leaves its contents behind (each call clears what must start at zero), so
+ * calls that overlap on the GPU -- on different streams or threads -- race;
+ * serialise them.  Errors: TM_EINVAL, TM_ENOMEM, TM_ECUDA, TM_EOVERFLOW;
+ * tm_last_error is not updated. */
+#define TM_NOALLOC_MAX_EDGES 262144
+#define TM_NOALLOC_SCRATCH_BYTES 7346688
+int tm_count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, void* stream,
+                           int64_t* count);
+
 /* ---- tuning ----------------------------------------------------------------
  * Matcher launch parameters.  0 keeps the current value.  The autotuner
  * (tm_autotune) writes these after timing candidates on a graph. */

@@ -21,6 +21,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "tm_internal.cuh"
@@ -1008,3 +1009,154 @@ int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* co
 }
 
 }  // namespace tmo
+
+// ---------------------------------------------------------------------------
+// Exact count without any allocation (tm_count_exact_noalloc).
+//
+// For callers that may not allocate device memory while answering a query:
+// the same kernels as the batched exact count, with every scratch buffer
+// (query plan, window descriptor and accumulators, per-first-edge ranges and
+// their scan, the work-queue counter, the result) carved out of one static
+// device array that the library carries for at most TM_NOALLOC_MAX_EDGES
+// edges.  Host code may not use the array's name as a device address, so the
+// address is resolved once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t na_a256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr int64_t kNaMaxEdges = TM_NOALLOC_MAX_EDGES;
+constexpr int64_t kNaWsElems = 2 * ((kNaMaxEdges + 2047) / 2048);
+constexpr size_t kNaWinBytes = 12 * 256 + na_a256(8 * tmo::A_N);
+constexpr size_t kNaBytes = na_a256(sizeof(tmo::QPlan)) + na_a256(sizeof(tm_result)) + kNaWinBytes +
+                            3 * 256 + na_a256(4 * kNaMaxEdges) + 3 * na_a256(8 * kNaMaxEdges) +
+                            na_a256(8 * kNaWsElems);
+static_assert(kNaBytes == TM_NOALLOC_SCRATCH_BYTES, "tm.h states the scratch size");
+constexpr int kNaMaxDevices = 64;
+
+std::mutex g_na_mu;
+unsigned char* g_na_base[kNaMaxDevices] = {};
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+namespace tmo {
+namespace {
+
+int na_status(cudaError_t e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TM_ENOMEM : TM_ECUDA;
+}
+
+// device address of the static scratch on the current device (resolved once per device)
+int na_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_status(e);
+    if (dev < 0 || dev >= kNaMaxDevices) return TM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_base[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return na_status(e);
+        g_na_base[dev] = (unsigned char*)p;
+    }
+    *out = g_na_base[dev];
+    return TM_OK;
+}
+
+int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cudaStream_t st,
+                        int64_t* count) {
+    if (!g || !m || !count) return TM_EINVAL;
+    if (delta < 0 || delta >= ((int64_t)1 << 61)) return TM_EINVAL;
+    if (g->m > kNaMaxEdges) return TM_EINVAL;
+    unsigned char* base = nullptr;
+    int rc = na_scratch(&base);
+    if (rc != TM_OK) return rc;
+    unsigned char* p = base;
+    auto take = [&](size_t bytes) { unsigned char* r = p; p += na_a256(bytes); return (void*)r; };
+    QPlan* dplan = (QPlan*)take(sizeof(QPlan));
+    tm_result* dres = (tm_result*)take(sizeof(tm_result));
+    WinDev W;
+    W.lo = (int64_t*)take(8);
+    W.hi = (int64_t*)take(8);
+    W.tend = (int64_t*)take(8);
+    W.start = (int64_t*)take(8);
+    W.j = (int64_t*)take(8);
+    W.nfirst = (int64_t*)take(8);
+    W.fbase = (int64_t*)take(8);
+    W.q = (int32_t*)take(4);
+    W.k = (int32_t*)take(4);
+    W.kept = (int32_t*)take(4);
+    W.qj = (double*)take(8);
+    take(8);  // keeps the window block at its documented size
+    W.acc = (unsigned long long*)take(8 * A_N);
+    int64_t* dF = (int64_t*)take(8);
+    int64_t* dW2 = (int64_t*)take(8);
+    unsigned long long* dctr = (unsigned long long*)take(8);
+    int32_t* fwin = (int32_t*)take(4 * (size_t)kNaMaxEdges);
+    int64_t* len2 = (int64_t*)take(8 * (size_t)kNaMaxEdges);
+    int64_t* lo2 = (int64_t*)take(8 * (size_t)kNaMaxEdges);
+    int64_t* excl = (int64_t*)take(8 * (size_t)kNaMaxEdges);
+    int64_t* ws = (int64_t*)take(8 * (size_t)kNaWsElems);
+    if ((size_t)(p - base) > kNaBytes) return TM_EINVAL;   // layout and array size disagree
+
+    tm_query q;
+    std::memset(&q, 0, sizeof(q));
+    q.motif = m;
+    q.delta = delta;
+    q.mode = TM_MODE_EXACT;
+    QPlan P;
+    fill_plan(P, q, g);
+    P.win_base = 0;
+    // every call starts from zeroed accumulators and queue counter
+    cudaError_t e = cudaMemcpyAsync(dplan, &P, sizeof(P), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(W.acc, 0, 8 * A_N, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dctr, 0, 8, st);
+    if (e != cudaSuccess) return na_status(e);
+    GraphDev G = g->dev;
+    k_windows<<<1, 32, 0, st>>>(G, dplan, 1, W, 1); count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return na_status(e);
+    rc = scan_exclusive_i64_ws(W.nfirst, W.fbase, 1, dF, ws, kNaWsElems, st);
+    if (rc != TM_OK) return rc;
+    int64_t F = g->m;   // one window holding every edge
+    if (F > 0) {
+        const Tuning tu = tuning();
+        MatchArgs A;
+        A.G = G; A.plans = dplan; A.nq = 1; A.W = W; A.NW = 1; A.F = F;
+        A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
+        A.enum_threshold = tu.enum_threshold;
+        A.chunk = tu.chunk_items;
+        int nsm = sm_count();
+        int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
+        k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, len2, lo2); count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return na_status(e);
+        rc = scan_exclusive_i64_ws(len2, excl, F, dW2, ws, kNaWsElems, st);
+        if (rc != TM_OK) return rc;
+        unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
+        if (P.l <= 4) k_match<4><<<gm, tu.block_threads, 0, st>>>(A);
+        else k_match<TM_L_MAX><<<gm, tu.block_threads, 0, st>>>(A);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return na_status(e);
+    }
+    k_fold<<<1, 256, 0, st>>>(dplan, W, dres); count_launch();
+    e = cudaGetLastError();
+    tm_result hres;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return na_status(e);
+    if (hres.status != TM_OK) return hres.status;
+    *count = hres.count;
+    return TM_OK;
+}
+
+}  // namespace
+}  // namespace tmo
+
+extern "C" int tm_count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, void* stream,
+                                      int64_t* count) {
+    return tmo::count_exact_noalloc(g, m, delta, (cudaStream_t)stream, count);
+}

@@ -221,6 +221,33 @@ int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* d_to
     return s1;
 }
 
+int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,
+                          int64_t* ws, int64_t ws_elems, cudaStream_t st) {
+    // Same result as scan_exclusive_i64, with the per-tile sums in the
+    // caller's workspace `ws` instead of a stream-ordered allocation.
+    if (n <= 0) {
+        if (d_total) {
+            k_set_i64<<<1, 1, 0, st>>>(d_total, 0); count_launch();
+            TM_CUDA(cudaGetLastError());
+        }
+        return TM_OK;
+    }
+    if (n <= kScanTile) {
+        k_scan_small<<<1, kScanThreads, 0, st>>>(in, out, n, d_total); count_launch();
+        TM_CUDA(cudaGetLastError());
+        return TM_OK;
+    }
+    int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > kScanTile || 2 * ntiles > ws_elems) return TM_EINVAL;
+    int64_t* sums = ws;
+    int64_t* soffs = ws + ntiles;
+    k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, n, sums); count_launch();
+    k_scan_small<<<1, kScanThreads, 0, st>>>(sums, soffs, ntiles, d_total); count_launch();
+    k_scan_add<<<(unsigned)ntiles, kScanThreads, 0, st>>>(out, n, soffs); count_launch();
+    TM_CUDA(cudaGetLastError());
+    return TM_OK;
+}
+
 int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                      int64_t n, int bits, cudaStream_t st) {
     // Sorts (keys, vals) stably by the low `bits` bits of keys; the result ends

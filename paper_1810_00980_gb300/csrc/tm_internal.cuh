@@ -137,6 +137,9 @@ int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* d_to
                        cudaStream_t st);
 int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                      int64_t n, int bits, cudaStream_t st);
+// exclusive scan with the tile sums in caller workspace (2 * ceil(n/2048) int64, n <= 2048^2)
+int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,
+                          int64_t* ws, int64_t ws_elems, cudaStream_t st);
 
 int sm_count();
 

@@ -88,6 +88,7 @@ _SIGS = {
     "tm_motif_free": (None, [_vp]),
     "tm_count_exact": (ctypes.c_int, [_vp, _vp, _c_i64, _vp]),
     "tm_count_exact_plain": (ctypes.c_int, [_vp, _vp, _c_i64, _vp]),
+    "tm_count_exact_noalloc": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "tm_estimate": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i32, _c_dbl, _c_u64, _vp]),
     "tm_estimate_windows": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i32, _c_dbl, _c_u64, _c_i32, _c_i32,
                                            _vp, _c_i64, _vp, _vp]),
@@ -231,6 +232,19 @@ def count_exact_plain(g: Graph, m: Motif, delta: int) -> int:
     out = _c_i64()
     _check(lib().tm_count_exact_plain(g.handle, m.handle, int(delta), ctypes.byref(out)),
            "tm_count_exact_plain")
+    return out.value
+
+
+NOALLOC_MAX_EDGES = 262144
+
+
+def count_exact_noalloc(g: Graph, m: Motif, delta: int, stream=None) -> int:
+    """tm_count_exact_noalloc: the exact count with no device allocation (static
+    scratch inside the library; graphs of at most NOALLOC_MAX_EDGES edges)."""
+    out = _c_i64()
+    st = 0 if stream is None else int(stream)
+    _check(lib().tm_count_exact_noalloc(g.handle, m.handle, int(delta), st, ctypes.byref(out)),
+           "tm_count_exact_noalloc")
     return out.value
 
 
