@@ -140,6 +140,28 @@ def make_queries(tm):
     return motifs, qs, meta
 
 
+# ----------------------------------------------------------- calibration ---
+def calibrate(tm, g, motifs, exact, seeds=64, target=0.05, q=0.95):
+    """For every (motif, delta): the cheapest (c, p, b) -- by b*p -- whose
+    relative error |Z - C|/C stays within `target` for a fraction q of
+    `seeds` independent seeds.  Prints one JSON line per (motif, delta)."""
+    cands = sorted(((c, p, b) for c in (2, 5, 10, 30) for p in (0.1, 0.2, 0.3, 0.5, 0.7, 0.85, 1.0)
+                    for b in (1, 2, 4)), key=lambda x: (x[1] * x[2], -x[0]))
+    for n in MOTIF_NAMES:
+        for d in DELTAS:
+            C = exact[(n, d)]
+            best = None
+            for (c, p, b) in cands:
+                qs = [tm.estimate_query(motifs[n], d, c, p, seed=50_000 + s, b=b) for s in range(seeds)]
+                rs = tm.run_batch(g, qs)
+                err = np.array([abs(r["estimate"] - C) / C for r in rs])
+                if np.quantile(err, q) <= target:
+                    best = (c, p, b, float(np.quantile(err, q)), float(err.mean()))
+                    break
+            print(json.dumps({"motif": n, "delta": d, "count": C, "c_p_b": best[:3] if best else None,
+                              "q95_err": best[3] if best else None, "mean_err": best[4] if best else None}))
+
+
 # --------------------------------------------------------- CPU baseline ---
 def cpu_baseline(src, dst, t, meta, frac=1 / 800, budget_s=25.0):
     """The oracle on a bounded sample: for every query, the first-edge prefix
@@ -229,6 +251,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="print the cheapest estimator parameters meeting 5%% error, then exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -269,6 +293,9 @@ def main():
         if k == "estimate":
             C = exact[(n, d)]
             rel_err[f"{n}@{d}"] = abs(r["estimate"] - C) / C if C else (0.0 if r["estimate"] == 0 else float("inf"))
+    if args.calibrate:
+        calibrate(tm, g0, motifs, exact)
+        return
     # one-query-per-launch plain exact counting (the baseline the batched form must beat)
     plain_qps = None
     if not args.no_plain:

@@ -113,6 +113,33 @@ __global__ void k_pair_index(const uint32_t* __restrict__ perm, const int32_t* _
     }
 }
 
+// Open-addressing hash of the static edges: key (src << 32 | dst) -> pair index.
+// Capacity is a power of two >= 2 P, so every probe chain ends at an empty slot.
+__global__ void k_hash_insert(const int32_t* __restrict__ pair_src, const int32_t* __restrict__ pair_dst,
+                              int64_t P, unsigned long long* __restrict__ slots, unsigned long long mask) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long key = ((unsigned long long)(uint32_t)pair_src[p] << 32) | (uint32_t)pair_dst[p];
+        unsigned long long h = sm64_mix(key) & mask;
+        for (unsigned long long it = 0; it <= mask; it++) {
+            unsigned long long prev = atomicCAS(&slots[2 * h], kHashEmpty, key);
+            if (prev == kHashEmpty) {
+                slots[2 * h + 1] = (unsigned long long)p;
+                break;
+            }
+            h = (h + 1) & mask;
+        }
+    }
+}
+
+__global__ void k_pair_src(const uint32_t* __restrict__ perm, const int32_t* __restrict__ src,
+                           const int64_t* __restrict__ head, const int64_t* __restrict__ pid_excl,
+                           int64_t m, int32_t* __restrict__ pair_src) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (head[i]) pair_src[pid_excl[i]] = src[perm[i]];
+}
+
 __global__ void k_pair_tail(int64_t* __restrict__ pair_off, const int64_t* __restrict__ P, int64_t m) {
     pair_off[*P] = m;
 }
@@ -178,7 +205,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     size_t total = 2 * sz_i32m + sz_i64m        // src, dst, t
                  + sz_off + sz_i32m + sz_i64m   // out view
                  + sz_off + sz_i32m + sz_i64m   // in view
-                 + sz_off + sz_i32m + align256(8 * (M + 1)) + sz_i64m;  // pair view (P <= m)
+                 + sz_off + sz_i32m + align256(8 * (M + 1)) + sz_i64m   // pair view (P <= m)
+                 + 2 * sz_i32m;                                          // view keys
     tm_graph* g = new (std::nothrow) tm_graph();
     if (!g) { set_error("host allocation failed"); return TM_ENOMEM; }
     g->device = dev;
@@ -187,7 +215,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     g->t_min = tmin;
     g->t_max = tmax;
     g->bytes = (int64_t)total;
-    cudaError_t e = cudaMalloc(&g->block, total);
+    pool_prepare(dev);
+    cudaError_t e = cudaMallocAsync(&g->block, total, st);
     if (e != cudaSuccess) {
         delete g;
         return cuda_status(e, "cudaMalloc(graph)", __FILE__, __LINE__);
@@ -207,6 +236,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     int32_t* pair_dst = (int32_t*)take(sz_i32m);
     int64_t* pair_off = (int64_t*)take(align256(8 * (M + 1)));
     int64_t* pair_t = (int64_t*)take(sz_i64m);
+    int32_t* out_src = (int32_t*)take(sz_i32m);
+    int32_t* in_dst = (int32_t*)take(sz_i32m);
 
     GraphDev& G = g->dev;
     G.m = m; G.n = n;
@@ -214,6 +245,9 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     G.out_off = out_off; G.out_nbr = out_nbr; G.out_t = out_t;
     G.in_off = in_off; G.in_nbr = in_nbr; G.in_t = in_t;
     G.pk_off = pk_off; G.pair_dst = pair_dst; G.pair_off = pair_off; G.pair_t = pair_t;
+    G.out_src = out_src; G.in_dst = in_dst;
+    G.hslots = nullptr; G.hmask = 0;
+    g->hash_block = nullptr;
 
     int rc = TM_OK;
     if (m == 0) {
@@ -235,7 +269,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     char* sb = nullptr;
     e = cudaMallocAsync((void**)&sb, scratch, st);
     if (e != cudaSuccess) {
-        cudaFree(g->block);
+        cudaStreamSynchronize(st);
+        pool_free(g->block, dev);
         delete g;
         return cuda_status(e, "cudaMallocAsync(graph scratch)", __FILE__, __LINE__);
     }
@@ -261,6 +296,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(ks, m, n, out_off); count_launch();
         k_gather_view<<<gr, kThreads, 0, st>>>(va, gd, gt, m, out_nbr, out_t); count_launch();
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        if (rc == TM_OK && cudaMemcpyAsync(out_src, ks, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = TM_ECUDA;
     }
     // in view: stably sorted by destination
     if (rc == TM_OK) rc = radix_sort_pairs(kd, vb, kt, vt, m, bits, st);
@@ -268,6 +305,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kd, m, n, in_off); count_launch();
         k_gather_view<<<gr, kThreads, 0, st>>>(vb, gs, gt, m, in_nbr, in_t); count_launch();
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        if (rc == TM_OK && cudaMemcpyAsync(in_dst, kd, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = TM_ECUDA;
     }
     // pair view: the in-view order stably re-sorted by source = (src, dst, time)
     if (rc == TM_OK) {
@@ -284,20 +323,43 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         k_pair_index<<<gr, kThreads, 0, st>>>(vb, gd, head, pid, m, pair_dst, pair_off); count_launch();
         k_pair_tail<<<1, 1, 0, st>>>(pair_off, dP, m); count_launch();
         k_pk_off<<<grid_for((int64_t)n + 1), kThreads, 0, st>>>(out_off, head, pid, dP, m, n, pk_off); count_launch();
+        k_pair_src<<<gr, kThreads, 0, st>>>(vb, gs, head, pid, m, (int32_t*)kt); count_launch();
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
     }
     int64_t P = 0;
     if (rc == TM_OK) {
         e = cudaMemcpyAsync(&P, dP, 8, cudaMemcpyDeviceToHost, st);
-        int ev1 = pe.mark(st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_status(e, "graph build", __FILE__, __LINE__);
-        if (rc == TM_OK && pe.on) store_profile_graph(pe.ms(ev0, ev1));
+    }
+    // pair hash: capacity the next power of two >= 2 P
+    if (rc == TM_OK) {
+        unsigned long long cap = 2;
+        while (cap < 2ull * (unsigned long long)P) cap <<= 1;
+        e = cudaMallocAsync(&g->hash_block, 16 * cap, st);
+        if (e != cudaSuccess) rc = cuda_status(e, "cudaMalloc(pair hash)", __FILE__, __LINE__);
+        if (rc == TM_OK) {
+            g->bytes += (int64_t)(16 * cap);
+            G.hslots = (const unsigned long long*)g->hash_block;
+            G.hmask = cap - 1;
+            e = cudaMemsetAsync(g->hash_block, 0xff, 16 * cap, st);
+            if (e == cudaSuccess) {
+                k_hash_insert<<<grid_for(P), kThreads, 0, st>>>((const int32_t*)kt, pair_dst, P,
+                                                               (unsigned long long*)g->hash_block, cap - 1);
+                count_launch();
+                e = cudaGetLastError();
+            }
+            int ev1 = pe.mark(st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = cuda_status(e, "pair hash build", __FILE__, __LINE__);
+            if (rc == TM_OK && pe.on) store_profile_graph(pe.ms(ev0, ev1));
+        }
     }
     cudaFreeAsync(sb, st);
     if (rc != TM_OK) {
         cudaStreamSynchronize(st);
-        cudaFree(g->block);
+        pool_free(g->block, dev);
+        pool_free(g->hash_block, dev);
         delete g;
         return rc;
     }
@@ -347,7 +409,8 @@ int tm_graph_load(const int32_t* src, const int32_t* dst, const int64_t* t, int6
 
 void tm_graph_free(tm_graph* g) {
     if (!g) return;
-    if (g->block) cudaFree(g->block);
+    tmo::pool_free(g->block, g->device);
+    tmo::pool_free(g->hash_block, g->device);
     delete g;
 }
 

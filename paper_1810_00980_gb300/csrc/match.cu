@@ -66,6 +66,8 @@ struct MatchArgs {
     const int32_t* fwin;   // [F] window of each first edge
     const int64_t* lo2;    // [F] start of its second-edge candidate range
     const int64_t* excl;   // [F] exclusive scan of the range lengths
+    const int64_t* hs_a;   // [F] closing pair range start (queries whose last edge is fixed by the first)
+    const int64_t* hs_hi;  // [F] closing pair range end
     const int64_t* d_W2;   // total second-edge candidates
     unsigned long long* counter;
     int64_t chunk;
@@ -95,15 +97,36 @@ __device__ __forceinline__ bool phi_has(const int32_t (&phi)[K], int nb, int32_t
     return r;
 }
 
-// time-sorted entries of the (u -> v) pair: [a, b) of pair_t
+// first index in [lo, hi) with a[idx] > v, by exponential then binary search
+// from lo: about 2 log2(answer - lo) probes, cheap when the answer is near lo
+__device__ __forceinline__ int64_t gallop_ub(const int64_t* __restrict__ a, int64_t lo, int64_t hi,
+                                             int64_t v) {
+    int64_t cur = lo, step = 1;
+    while (cur < hi && __ldg(a + cur) <= v) {
+        lo = cur + 1;
+        cur += step;
+        step <<= 1;
+    }
+    if (cur > hi) cur = hi;
+    return upper_bound_i64(a, lo, cur, v);
+}
+
+// time-sorted entries of the (u -> v) pair: [a, b) of pair_t, through the
+// open-addressing hash of static edges (probe chains end at an empty slot)
 __device__ __forceinline__ bool pair_segment(const GraphDev& G, int32_t u, int32_t v, int64_t& a,
                                              int64_t& b) {
-    int64_t lo = __ldg(G.pk_off + u), hi = __ldg(G.pk_off + u + 1);
-    int64_t p = lower_bound_i32(G.pair_dst, lo, hi, v);
-    if (p < hi && __ldg(G.pair_dst + p) == v) {
-        a = __ldg(G.pair_off + p);
-        b = __ldg(G.pair_off + p + 1);
-        return true;
+    unsigned long long key = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
+    unsigned long long h = sm64_mix(key) & G.hmask;
+    for (unsigned long long it = 0; it <= G.hmask; it++) {
+        unsigned long long k = __ldg(G.hslots + 2 * h);
+        if (k == key) {
+            int64_t p = (int64_t)__ldg(G.hslots + 2 * h + 1);
+            a = __ldg(G.pair_off + p);
+            b = __ldg(G.pair_off + p + 1);
+            return true;
+        }
+        if (k == kHashEmpty) break;
+        h = (h + 1) & G.hmask;
     }
     a = b = 0;
     return false;
@@ -112,9 +135,9 @@ __device__ __forceinline__ bool pair_segment(const GraphDev& G, int32_t u, int32
 __device__ __forceinline__ int64_t pair_count(const GraphDev& G, int32_t u, int32_t v, int64_t tprev,
                                               int64_t thi) {
     int64_t a, b;
-    if (!pair_segment(G, u, v, a, b)) return 0;
+    if (thi <= tprev || !pair_segment(G, u, v, a, b)) return 0;
     int64_t lo = upper_bound_i64(G.pair_t, a, b, tprev);
-    int64_t hi = upper_bound_i64(G.pair_t, lo, b, thi);
+    int64_t hi = gallop_ub(G.pair_t, lo, b, thi);
     return hi - lo;
 }
 
@@ -126,9 +149,12 @@ __device__ __forceinline__ void level_range(const GraphDev& G, const LevelPlan& 
                                             int64_t& lo, int64_t& len) {
     const int64_t* ta;
     int64_t a, b;
+    lo = 0;
+    len = 0;
+    if (thi <= tprev) return;
     if (P.view == kPair) {
         ta = G.pair_t;
-        if (!pair_segment(G, phi_get(phi, P.su), phi_get(phi, P.sv), a, b)) { lo = 0; len = 0; return; }
+        if (!pair_segment(G, phi_get(phi, P.su), phi_get(phi, P.sv), a, b)) return;
     } else if (P.view == kOut) {
         int32_t u = phi_get(phi, P.su);
         ta = G.out_t; a = __ldg(G.out_off + u); b = __ldg(G.out_off + u + 1);
@@ -138,10 +164,8 @@ __device__ __forceinline__ void level_range(const GraphDev& G, const LevelPlan& 
     } else {
         ta = G.t; a = 0; b = G.m;
     }
-    if (thi <= tprev) { lo = a; len = 0; return; }
     lo = upper_bound_i64(ta, a, b, tprev);
-    int64_t hi = upper_bound_i64(ta, lo, b, thi);
-    len = hi - lo;
+    len = gallop_ub(ta, lo, b, thi) - lo;
 }
 
 // read candidate c of the view; returns its (src, dst, time)
@@ -157,6 +181,18 @@ __device__ __forceinline__ void read_cand(const GraphDev& G, const LevelPlan& P,
         s = __ldg(G.in_nbr + c); d = phi_get(phi, P.sv); tc = __ldg(G.in_t + c);
     } else {
         s = __ldg(G.src + c); d = __ldg(G.dst + c); tc = __ldg(G.t + c);
+    }
+}
+
+// the first edge at position e of the order the query enumerates first edges in
+__device__ __forceinline__ void first_edge(const GraphDev& G, int order, int64_t e, int32_t& s,
+                                           int32_t& d, int64_t& t) {
+    if (order == kOrdOut) {
+        s = __ldg(G.out_src + e); d = __ldg(G.out_nbr + e); t = __ldg(G.out_t + e);
+    } else if (order == kOrdIn) {
+        s = __ldg(G.in_nbr + e); d = __ldg(G.in_dst + e); t = __ldg(G.in_t + e);
+    } else {
+        s = __ldg(G.src + e); d = __ldg(G.dst + e); t = __ldg(G.t + e);
     }
 }
 
@@ -267,26 +303,46 @@ __device__ __forceinline__ void acc_switch(Acc& a, int64_t win, unsigned long lo
     }
 }
 
+// c delta / (c delta - dur) in Q64 by long division (64 fraction bits, rounded down)
+__device__ __forceinline__ void q64_weight(int64_t cd, int64_t dur, unsigned long long& wi,
+                                        unsigned long long& wf) {
+    unsigned long long D = (unsigned long long)(cd - dur);
+    unsigned long long N = (unsigned long long)cd;
+    wi = N / D;
+    unsigned long long r = N - wi * D;
+    wf = 0;
+    for (int i = 0; i < 64; i++) {
+        r <<= 1;
+        wf <<= 1;
+        if (r >= D) { r -= D; wf |= 1; }
+    }
+}
+
 __device__ __forceinline__ void add_weight(Acc& a, const QPlan& Q, int64_t dur) {
     unsigned long long wi, wf;
     if (Q.wtab) {
         wi = __ldg(Q.wtab + 2 * dur);
         wf = __ldg(Q.wtab + 2 * dur + 1);
     } else {
-        // c delta / (c delta - dur) by long division, 64 fraction bits
-        unsigned long long D = (unsigned long long)(Q.cd - dur);
-        unsigned long long N = (unsigned long long)Q.cd;
-        wi = N / D;
-        unsigned long long r = N - wi * D;
-        wf = 0;
-        for (int i = 0; i < 64; i++) {
-            r <<= 1;
-            wf <<= 1;
-            if (r >= D) { r -= D; wf |= 1; }
-        }
+        q64_weight(Q.cd, dur, wi, wf);
     }
     unsigned long long s = a.f[A_WLO] + wf;
     a.f[A_WHI] += wi + (s < wf ? 1ull : 0ull);
+    a.f[A_WLO] = s;
+}
+
+// n instances of duration dur at once: n * (wi + wf 2^-64), exactly as n single adds
+__device__ __forceinline__ void add_weight_n(Acc& a, const QPlan& Q, int64_t dur, unsigned long long n) {
+    unsigned long long wi, wf;
+    if (Q.wtab) {
+        wi = __ldg(Q.wtab + 2 * dur);
+        wf = __ldg(Q.wtab + 2 * dur + 1);
+    } else {
+        q64_weight(Q.cd, dur, wi, wf);
+    }
+    unsigned long long lo = wf * n, hi = __umul64hi(wf, n);
+    unsigned long long s = a.f[A_WLO] + lo;
+    a.f[A_WHI] += wi * n + hi + (s < lo ? 1ull : 0ull);
     a.f[A_WLO] = s;
 }
 
@@ -363,7 +419,8 @@ __global__ void k_windows(GraphDev G, const QPlan* __restrict__ plans, int nq, W
 
 // one warp-uniform grid-stride loop over first edges f
 __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict__ fwin,
-                                                int64_t* __restrict__ len2, int64_t* __restrict__ lo2) {
+                                                int64_t* __restrict__ len2, int64_t* __restrict__ lo2,
+                                                int64_t* __restrict__ hs_a, int64_t* __restrict__ hs_hi) {
     const GraphDev& G = A.G;
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -392,23 +449,58 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict
         if (!valid) continue;
         const QPlan& Q = A.plans[A.W.q[wi]];
         int64_t e1 = A.W.lo[wi] + (f - A.W.fbase[wi]);
-        int32_t s1 = __ldg(G.src + e1), d1 = __ldg(G.dst + e1);
-        int64_t t1 = __ldg(G.t + e1);
+        int32_t s1, d1;
+        int64_t t1;
+        first_edge(G, Q.order, e1, s1, d1, t1);
         int64_t thi = min(t1 + Q.delta, A.W.tend[wi]);
-        int64_t len = 0, lo = 0;
+        int64_t len = 0, lo = 0, ha = 0, hh = 0;
         acc.f[A_FIRST] += 1;
         if (s1 != d1) {
             if (Q.l == 1) {
                 acc.f[A_COUNT] += 1;
                 if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, 0);
             } else {
-                int32_t phi[TM_K_MAX];
-#pragma unroll
-                for (int i = 0; i < TM_K_MAX; i++) phi[i] = -1;
-                phi[0] = s1;
-                phi[1] = d1;
+                int32_t phi[2] = {s1, d1};
                 const LevelPlan P = Q.lv[1];
-                level_range(G, P, phi, t1, thi, lo, len);
+                if (Q.order == kOrdOut && P.view == kOut && P.su == 0) {
+                    // e1 is entry e1 of out(s1): its candidates start right after it
+                    int64_t b = __ldg(G.out_off + s1 + 1);
+                    lo = gallop_ub(G.out_t, e1 + 1, b, t1);
+                    len = thi > t1 ? gallop_ub(G.out_t, lo, b, thi) - lo : 0;
+                } else if (Q.order == kOrdIn && P.view == kIn && P.sv == 1) {
+                    int64_t b = __ldg(G.in_off + d1 + 1);
+                    lo = gallop_ub(G.in_t, e1 + 1, b, t1);
+                    len = thi > t1 ? gallop_ub(G.in_t, lo, b, thi) - lo : 0;
+                } else {
+                    level_range(G, P, phi, t1, thi, lo, len);
+                }
+                if (Q.rev && len > 0) {
+                    // candidates of the last edge given only its first-edge node
+                    const LevelPlan L = Q.lv[2];
+                    bool x_src = L.su == 2;
+                    int32_t bn = x_src ? phi_get(phi, L.sv) : phi_get(phi, L.su);
+                    const int64_t* ta = x_src ? G.in_t : G.out_t;
+                    const int64_t* off = x_src ? G.in_off : G.out_off;
+                    int64_t a = __ldg(off + bn), b = __ldg(off + bn + 1);
+                    int64_t rlo = upper_bound_i64(ta, a, b, t1);
+                    int64_t rlen = gallop_ub(ta, rlo, b, thi) - rlo;
+                    if (rlen == 0) {
+                        len = 0;                 // nothing can close an instance
+                    } else if (rlen < len) {
+                        lo = -1 - rlo;           // negative: items are last-edge candidates
+                        len = rlen;
+                    }
+                }
+                if (Q.hoist && len > 0) {
+                    // the closing pair is fixed by the first edge: find its range once
+                    const LevelPlan L = Q.lv[Q.l - 1];
+                    int64_t a0, b0;
+                    if (pair_segment(G, phi_get(phi, L.su), phi_get(phi, L.sv), a0, b0)) {
+                        ha = upper_bound_i64(G.pair_t, a0, b0, t1);
+                        hh = gallop_ub(G.pair_t, ha, b0, thi);
+                    }
+                    if (hh == ha) len = 0;   // no closing edge in time: no instance starts here
+                }
                 if (Q.l == 2 && Q.mode == TM_MODE_EXACT) {
                     if (P.view == kPair) {
                         acc.f[A_COUNT] += len;
@@ -425,22 +517,33 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict
         fwin[f] = (int32_t)wi;
         len2[f] = len;
         lo2[f] = lo;
+        if (hs_a) {
+            hs_a[f] = ha;
+            hs_hi[f] = hh;
+        }
     }
     acc_flush_warp(acc, A.W.acc);
 }
 
 // Warp-cooperative expansion of motif edge D (0-based) for the 32 partial
 // instances held by the lanes (valid ones have edges 0..D-1 matched).
-template <int D, int LMAX>
+// (ha, hh): the closing pair range when the query fixed it at the first edge.
+template <int D, int LMAX, int KMAX>
 __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
-                       int32_t (&phi)[TM_K_MAX], int64_t t1, int64_t tprev, int64_t thi, Acc& acc) {
+                       int32_t (&phi)[KMAX], int64_t t1, int64_t tprev, int64_t thi, int64_t ha,
+                       int64_t hh, Acc& acc) {
     const GraphDev& G = A.G;
     int lane = threadIdx.x & 31;
     int64_t lo = 0, len = 0;
     if (valid) {
         const QPlan& Q = A.plans[q];
         const LevelPlan P = Q.lv[D];
-        level_range(G, P, phi, tprev, thi, lo, len);
+        if (D == Q.l - 1 && Q.hoist) {
+            lo = upper_bound_i64(G.pair_t, ha, hh, tprev);
+            len = hh - lo;
+        } else {
+            level_range(G, P, phi, tprev, thi, lo, len);
+        }
         if (D == Q.l - 1) {
             acc_switch(acc, win, A.W.acc);
             acc.f[A_LAST] += 1;
@@ -474,9 +577,11 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
         int64_t ost = __shfl_sync(kFull, mystart, o);
         int64_t ot1 = __shfl_sync(kFull, t1, o);
         int64_t othi = __shfl_sync(kFull, thi, o);
-        int32_t ophi[TM_K_MAX];
+        int64_t oha = __shfl_sync(kFull, ha, o);
+        int64_t ohh = __shfl_sync(kFull, hh, o);
+        int32_t ophi[KMAX];
 #pragma unroll
-        for (int i = 0; i < TM_K_MAX; i++) ophi[i] = __shfl_sync(kFull, phi[i], o);
+        for (int i = 0; i < KMAX; i++) ophi[i] = __shfl_sync(kFull, phi[i], o);
         bool ok = false, deeper = false;
         int64_t tc = 0;
         if (has) {
@@ -485,27 +590,26 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
             int32_t s, d;
             read_cand(G, P, ophi, olo + (x - ost), s, d, tc);
             ok = check_bind(P, ophi, s, d);
+            acc_switch(acc, ow, A.W.acc);
             if (D == Q.l - 1) {
-                acc_switch(acc, ow, A.W.acc);
                 acc.f[A_INST] += 1;
                 if (ok) {
                     acc.f[A_COUNT] += 1;
                     if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - ot1);
                 }
             } else {
-                acc_switch(acc, ow, A.W.acc);
                 acc.f[A_CAND] += 1;
                 deeper = ok;
             }
         }
         if constexpr (D + 1 < LMAX) {
             if (__any_sync(kFull, deeper))
-                expand<D + 1, LMAX>(A, deeper, oq, ow, ophi, ot1, tc, othi, acc);
+                expand<D + 1, LMAX, KMAX>(A, deeper, oq, ow, ophi, ot1, tc, othi, oha, ohh, acc);
         }
     }
 }
 
-template <int LMAX>
+template <int LMAX, int KMAX>
 __global__ void __launch_bounds__(256) k_match(MatchArgs A) {
     const GraphDev& G = A.G;
     int lane = threadIdx.x & 31;
@@ -530,10 +634,10 @@ __global__ void __launch_bounds__(256) k_match(MatchArgs A) {
             int64_t w = base + lane;
             bool valid = w < c1;
             int32_t q = 0;
-            int64_t win = -1, t1 = 0, thi = 0, tc = 0;
-            int32_t phi[TM_K_MAX];
+            int64_t win = -1, t1 = 0, thi = 0, tc = 0, ha = 0, hh = 0;
+            int32_t phi[KMAX];
 #pragma unroll
-            for (int i = 0; i < TM_K_MAX; i++) phi[i] = -1;
+            for (int i = 0; i < KMAX; i++) phi[i] = -1;
             bool deeper = false;
             if (valid) {
                 int64_t f = upper_bound_i64(A.excl, fb, fe + 1, w) - 1;
@@ -541,14 +645,38 @@ __global__ void __launch_bounds__(256) k_match(MatchArgs A) {
                 q = A.W.q[win];
                 const QPlan& Q = A.plans[q];
                 int64_t e1 = A.W.lo[win] + (f - A.W.fbase[win]);
-                phi[0] = __ldg(G.src + e1);
-                phi[1] = __ldg(G.dst + e1);
-                t1 = __ldg(G.t + e1);
+                first_edge(G, Q.order, e1, phi[0], phi[1], t1);
                 thi = min(t1 + Q.delta, A.W.tend[win]);
+                int64_t l2 = A.lo2[f];
+                if (l2 < 0) {
+                    // closing-edge candidate e3 = (x, t3); count second edges in (t1, t3)
+                    const LevelPlan L = Q.lv[2];
+                    const LevelPlan M1 = Q.lv[1];
+                    int64_t c = (-1 - l2) + (w - A.excl[f]);
+                    bool x_src = L.su == 2;
+                    int32_t x = x_src ? __ldg(G.in_nbr + c) : __ldg(G.out_nbr + c);
+                    int64_t t3 = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
+                    acc_switch(acc, win, A.W.acc);
+                    acc.f[A_CAND] += 1;
+                    if (x != phi[0] && x != phi[1]) {
+                        int32_t mu = M1.su == 2 ? x : phi_get(phi, M1.su);
+                        int32_t mv = M1.sv == 2 ? x : phi_get(phi, M1.sv);
+                        int64_t cnt = pair_count(G, mu, mv, t1, t3 - 1);
+                        acc.f[A_LAST] += 1;
+                        if (cnt) {
+                            acc.f[A_COUNT] += cnt;
+                            if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                        }
+                    }
+                } else {
                 const LevelPlan P = Q.lv[1];
                 int32_t s, d;
-                read_cand(G, P, phi, A.lo2[f] + (w - A.excl[f]), s, d, tc);
+                read_cand(G, P, phi, l2 + (w - A.excl[f]), s, d, tc);
                 bool ok = check_bind(P, phi, s, d);
+                if (Q.hoist) {
+                    ha = A.hs_a[f];
+                    hh = A.hs_hi[f];
+                }
                 acc_switch(acc, win, A.W.acc);
                 if (Q.l == 2) {
                     acc.f[A_INST] += 1;
@@ -558,11 +686,21 @@ __global__ void __launch_bounds__(256) k_match(MatchArgs A) {
                     }
                 } else {
                     acc.f[A_CAND] += 1;
-                    deeper = ok;
+                    const LevelPlan L = Q.lv[2];
+                    if (ok && Q.l == 3 && Q.mode == TM_MODE_EXACT && L.view == kPair) {
+                        // close the instance here: the last edge is counted by range length
+                        int64_t cnt = Q.hoist ? hh - upper_bound_i64(G.pair_t, ha, hh, tc)
+                                              : pair_count(G, phi_get(phi, L.su), phi_get(phi, L.sv), tc, thi);
+                        acc.f[A_COUNT] += cnt;
+                        acc.f[A_LAST] += 1;
+                    } else {
+                        deeper = ok;
+                    }
+                }
                 }
             }
             if (__any_sync(kFull, deeper))
-                expand<2, LMAX>(A, deeper, q, win, phi, t1, tc, thi, acc);
+                expand<2, LMAX, KMAX>(A, deeper, q, win, phi, t1, tc, thi, ha, hh, acc);
         }
         acc_flush_warp(acc, A.W.acc);
     }
@@ -746,8 +884,29 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
     P.mode = q.mode;
     P.delta = q.delta;
     for (int i = 0; i < TM_L_MAX; i++) P.lv[i] = m->lv[i];
+    P.order = kOrdTime;
+    P.hoist = 0;
+    P.rev = 0;
+    if (m->l >= 3) {
+        const LevelPlan& L = m->lv[m->l - 1];
+        P.hoist = (L.view == kPair && L.su <= 1 && L.sv <= 1) ? 1 : 0;
+    }
+    if (m->l == 3) {
+        const LevelPlan& L1 = m->lv[1];
+        const LevelPlan& L2 = m->lv[2];
+        bool one_new = (L1.view == kOut || L1.view == kIn) && (L1.bind_u + L1.bind_v == 1);
+        bool closes_x = L2.view == kPair && ((L2.su == 2 && L2.sv <= 1) || (L2.sv == 2 && L2.su <= 1));
+        P.rev = (one_new && closes_x) ? 1 : 0;
+    }
     if (q.mode == TM_MODE_EXACT) {
         P.b = 1; P.cd = 0; P.J = 1; P.p = 1.0; P.q_mode = TM_Q_UNIFORM;
+        // exact queries take first edges grouped by the node their second edge hangs off
+        if (m->l >= 2) {
+            const LevelPlan& L1 = m->lv[1];
+            if (L1.view == kOut) P.order = L1.su == 0 ? kOrdOut : kOrdIn;
+            else if (L1.view == kIn) P.order = L1.sv == 1 ? kOrdIn : kOrdOut;
+            else if (L1.view == kPair) P.order = L1.su == 0 ? kOrdOut : kOrdIn;
+        }
     } else {
         P.b = q.b;
         P.cd = (int64_t)q.c * q.delta;
@@ -769,7 +928,8 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
     std::vector<int> qstat((size_t)nq, TM_OK);
     int first_err = TM_OK;
     int64_t NW = 0;
-    int lmax = 1;
+    int lmax = 1, kmax = 2;
+    bool any_hoist = false;
     size_t wtab_bytes = 0;
     for (int i = 0; i < nq; i++) {
         std::string why;
@@ -787,6 +947,8 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
         hp[(size_t)i].win_base = NW;
         NW += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].J * hp[(size_t)i].b;
         lmax = std::max(lmax, hp[(size_t)i].l);
+        kmax = std::max(kmax, hp[(size_t)i].k);
+        any_hoist |= hp[(size_t)i].hoist != 0;
         if (hp[(size_t)i].mode == TM_MODE_ESTIMATE && hp[(size_t)i].delta + 1 <= kWtabMax)
             wtab_bytes += a256(16 * (size_t)(hp[(size_t)i].delta + 1));
     }
@@ -860,31 +1022,36 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
     char* fb = nullptr;
     if (rc == TM_OK && F > 0) {
         size_t Fs = (size_t)F;
-        fail(cudaMallocAsync((void**)&fb, a256(4 * Fs) + 3 * a256(8 * Fs), st), "per-edge scratch");
+        fail(cudaMallocAsync((void**)&fb, a256(4 * Fs) + (any_hoist ? 5 : 3) * a256(8 * Fs), st),
+             "per-edge scratch");
         if (rc == TM_OK) {
             char* q2 = fb;
             auto take2 = [&](size_t bytes) { char* r = q2; q2 += a256(bytes); return (void*)r; };
             int32_t* fwin = (int32_t*)take2(4 * Fs);
-            int64_t* len2 = (int64_t*)take2(8 * Fs);
             int64_t* lo2 = (int64_t*)take2(8 * Fs);
-            int64_t* excl = (int64_t*)take2(8 * Fs);
+            int64_t* excl = (int64_t*)take2(8 * Fs);   // range lengths, then their exclusive scan in place
+            int64_t* hs_a = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
+            int64_t* hs_hi = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             MatchArgs A;
             A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = F;
-            A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
+            A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
+            A.d_W2 = dW2; A.counter = dctr;
             A.enum_threshold = tu.enum_threshold;
             int bt = tu.block_threads;
-            int64_t gl2 = std::min<int64_t>((F + bt - 1) / bt, (int64_t)nsm * 8);
+            int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
             ev_l0 = pe.mark(st);
-            k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, len2, lo2); count_launch();
+            k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
             fail(cudaGetLastError(), "k_level2");
-            if (rc == TM_OK) rc = scan_exclusive_i64(len2, excl, F, dW2, st);
+            if (rc == TM_OK) rc = scan_exclusive_i64(excl, excl, F, dW2, st);
             ev_l1 = pe.mark(st);
             if (rc == TM_OK) {
                 int bps = tu.blocks_per_sm;
                 A.chunk = tu.chunk_items;
                 unsigned gm = (unsigned)(nsm * bps);
-                if (lmax <= 4) k_match<4><<<gm, bt, 0, st>>>(A);
-                else k_match<TM_L_MAX><<<gm, bt, 0, st>>>(A);
+                if (lmax <= 3 && kmax <= 4) k_match<3, 4><<<gm, bt, 0, st>>>(A);
+                else if (lmax <= 4 && kmax <= 4) k_match<4, 4><<<gm, bt, 0, st>>>(A);
+                else if (lmax <= 4) k_match<4, TM_K_MAX><<<gm, bt, 0, st>>>(A);
+                else k_match<TM_L_MAX, TM_K_MAX><<<gm, bt, 0, st>>>(A);
                 count_launch();
                 fail(cudaGetLastError(), "k_match");
                 ev_m1 = pe.mark(st);
@@ -1109,6 +1276,7 @@ int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cud
     QPlan P;
     fill_plan(P, q, g);
     P.win_base = 0;
+    P.hoist = 0;   // no per-first-edge closing ranges: keeps the scratch at its stated size
     // every call starts from zeroed accumulators and queue counter
     cudaError_t e = cudaMemcpyAsync(dplan, &P, sizeof(P), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(W.acc, 0, 8 * A_N, st);
@@ -1126,18 +1294,22 @@ int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cud
         MatchArgs A;
         A.G = G; A.plans = dplan; A.nq = 1; A.W = W; A.NW = 1; A.F = F;
         A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
+        A.hs_a = nullptr; A.hs_hi = nullptr;
         A.enum_threshold = tu.enum_threshold;
         A.chunk = tu.chunk_items;
         int nsm = sm_count();
         int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
-        k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, len2, lo2); count_launch();
+        k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, len2, lo2, nullptr, nullptr);
+        count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
         rc = scan_exclusive_i64_ws(len2, excl, F, dW2, ws, kNaWsElems, st);
         if (rc != TM_OK) return rc;
         unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
-        if (P.l <= 4) k_match<4><<<gm, tu.block_threads, 0, st>>>(A);
-        else k_match<TM_L_MAX><<<gm, tu.block_threads, 0, st>>>(A);
+        if (P.l <= 3 && P.k <= 4) k_match<3, 4><<<gm, tu.block_threads, 0, st>>>(A);
+        else if (P.l <= 4 && P.k <= 4) k_match<4, 4><<<gm, tu.block_threads, 0, st>>>(A);
+        else if (P.l <= 4) k_match<4, TM_K_MAX><<<gm, tu.block_threads, 0, st>>>(A);
+        else k_match<TM_L_MAX, TM_K_MAX><<<gm, tu.block_threads, 0, st>>>(A);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);

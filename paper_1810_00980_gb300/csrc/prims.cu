@@ -2,6 +2,7 @@
 // (uint32 key, uint32 value) pairs.  Neither waits on other blocks: the scan
 // is reduce-then-scan over tiles, the sort is histogram / scan / scatter per
 // digit, so no launch can spin.
+#include <mutex>
 #include <vector>
 
 #include "tm_internal.cuh"
@@ -45,8 +46,8 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* smem, int
 }
 
 // Each block scans one tile (exclusive), writes the tile total to sums[tile].
-__global__ void k_scan_tiles(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
-                             int64_t* __restrict__ sums) {
+// (in may equal out: every thread reads its items before any thread writes)
+__global__ void k_scan_tiles(const int64_t* in, int64_t* out, int64_t n, int64_t* __restrict__ sums) {
     __shared__ int64_t smem[33];
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
@@ -77,8 +78,7 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
     }
 }
 
-__global__ void k_scan_small(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
-                             int64_t* __restrict__ d_total) {
+__global__ void k_scan_small(const int64_t* in, int64_t* out, int64_t n, int64_t* __restrict__ d_total) {
     // single block, n <= kScanTile
     __shared__ int64_t smem[33];
     int64_t base = (int64_t)threadIdx.x * kScanItems;
@@ -287,6 +287,36 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_
     cudaFreeAsync(offs, st);
     if (rc != TM_OK) set_error("radix sort launch failed");
     return rc;
+}
+
+namespace {
+std::mutex g_pool_mu;
+bool g_pool_ready[64] = {};
+cudaStream_t g_free_stream[64] = {};
+}  // namespace
+
+int pool_prepare(int dev) {
+    if (dev < 0 || dev >= 64) return TM_OK;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_ready[dev]) return TM_OK;
+    // keep freed blocks of the device's default pool mapped, so that graphs and
+    // batch scratch that come and go reuse memory instead of remapping it
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaStreamCreateWithFlags(&g_free_stream[dev], cudaStreamNonBlocking);
+    cudaGetLastError();
+    g_pool_ready[dev] = true;
+    return TM_OK;
+}
+
+void pool_free(void* p, int dev) {
+    if (!p) return;
+    cudaStream_t s = (dev >= 0 && dev < 64) ? g_free_stream[dev] : nullptr;
+    if (s) cudaFreeAsync(p, s);
+    else cudaFree(p);
 }
 
 int sm_count() {

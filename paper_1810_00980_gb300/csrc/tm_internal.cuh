@@ -51,7 +51,13 @@ struct GraphDev {
     const int32_t* pair_dst;// [P]
     const int64_t* pair_off;// [P+1]
     const int64_t* pair_t;  // [m]
+    const int32_t* out_src; // [m] source of each out-view entry (the sort key)
+    const int32_t* in_dst;  // [m] destination of each in-view entry
+    const unsigned long long* hslots;  // [2*(hmask+1)]: (key, pair index) per slot
+    unsigned long long hmask;          // hash capacity - 1 (power of two)
 };
+
+constexpr unsigned long long kHashEmpty = ~0ull;
 
 }  // namespace tmo
 
@@ -64,6 +70,7 @@ struct tm_graph {
     int64_t t_max;          // normalised
     int64_t bytes;
     void* block;            // one device allocation holding every array
+    void* hash_block;       // the (src, dst) -> pair index hash table
     tmo::GraphDev dev;
 };
 
@@ -94,12 +101,20 @@ struct tm_motif {
 
 namespace tmo {
 
+// order in which a query enumerates first edges: by time (windows), or grouped
+// by source / destination (positions of the out / in view) for exact queries
+enum FirstOrder : int32_t { kOrdTime = 0, kOrdOut = 1, kOrdIn = 2 };
+
 struct QPlan {
     int32_t l, k;
     int32_t mode;        // TM_MODE_*
     int32_t b;
     int32_t q_mode;
-    int32_t pad0;
+    int32_t order;       // FirstOrder
+    int32_t hoist;       // 1: the last motif edge joins the first edge's two nodes
+    int32_t rev;         // 1: three edges, the second binds one new node x and the last
+                         //    joins x to a first-edge node: instances can be closed from
+                         //    either the second or the last edge's candidates
     int64_t delta;
     int64_t cd;          // c * delta (estimate), 0 for exact
     int64_t J;           // windows per shift (estimate), 1 for exact
@@ -142,6 +157,10 @@ int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d
                           int64_t* ws, int64_t ws_elems, cudaStream_t st);
 
 int sm_count();
+// device memory pool (prims.cu): raise the default pool's release threshold once
+// per device; pool_free returns a stream-ordered block on an internal stream
+int pool_prepare(int dev);
+void pool_free(void* p, int dev);
 
 // profiling (abi.cu): phase events of the last batch / graph build, launch counter
 bool profiling();

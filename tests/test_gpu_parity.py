@@ -26,6 +26,9 @@ MOTIFS = [
     ([1, 0], [0, 2]),
     ([0, 2], [1, 1]),
     ([0, 1, 2], [1, 2, 0]),
+    ([0, 2, 2], [1, 1, 0]),          # a->b, c->b, c->a: closes from the last edge's side too
+    ([0, 1, 0], [1, 2, 2]),          # a->b, b->c, a->c
+    ([0, 0, 1], [1, 2, 2]),          # a->b, a->c, b->c
     ([2, 2, 2], [0, 1, 0]),
     ([0, 1, 0], [1, 0, 1]),
     ([0, 2, 1], [1, 3, 2]),
@@ -223,8 +226,8 @@ def test_config1_exact_and_estimate(tm, orc):
 def test_estimate_mid_graph_parity(tm, orc):
     src, dst, t = synth.chung_lu_hawkes(3000, 300_000, 2.1, seed=22, horizon=6_000_000)
     g = _graph(tm, src, dst, t)
-    for name in ("cycle3", "outstar3", "pingpong", "cycle4"):
-        ms, md = synth.MOTIFS[name]
+    for name in ("cycle3", "outstar3", "pingpong", "cycle4", "feedfwd3"):
+        ms, md = synth.MOTIFS[name] if name in synth.MOTIFS else ([0, 1, 0], [1, 2, 2])
         mo = tm.Motif(ms, md)
         for (delta, c, p, seed) in ((600, 10, 0.1, 1), (3600, 30, 0.3, 2), (3600, 2, 1.0, 3)):
             z = tm.estimate(g, mo, delta, c, p, seed)
