@@ -42,8 +42,15 @@ sys.path.insert(0, ROOT)
 METRIC = "queries/s, edges/s at <=5% rel. err vs plain exact GPU count; p50/p99 latency"
 MOTIF_NAMES = ("cycle3", "outstar3", "pingpong")
 DELTAS = (600, 3600, 86400)
-# estimator parameters per delta: (c, p, b)
-EST_PARAMS = {600: (30, 0.1, 1), 3600: (10, 0.1, 1), 86400: (2, 0.1, 1)}
+# estimator parameters (c, p, b) per (motif, delta): the cheapest (by b*p) found by
+# `TM_CAL_TARGET=0.035 bench.py --calibrate` whose relative error stayed within 3.5%
+# for 95% of 64 seeds (so within 5% with a wide margin).  At delta = 86,400 s on this
+# two-year graph only c = 30, p = 1 (every window, one shift) gets there.
+EST_PARAMS = {
+    ("cycle3", 600): (30, 0.85, 1), ("cycle3", 3600): (5, 0.7, 1), ("cycle3", 86400): (30, 1.0, 1),
+    ("outstar3", 600): (10, 0.2, 1), ("outstar3", 3600): (2, 0.1, 4), ("outstar3", 86400): (30, 1.0, 1),
+    ("pingpong", 600): (10, 0.2, 1), ("pingpong", 3600): (2, 0.3, 1), ("pingpong", 86400): (30, 1.0, 1),
+}
 SEED = 2
 
 
@@ -55,7 +62,7 @@ def peaks():
 
 
 def workload_desc():
-    est = ", ".join(f"delta={d}: c={c}, p={p}, b={b}" for d, (c, p, b) in EST_PARAMS.items())
+    est = ", ".join(f"{n}@{d}: c={c}, p={p}, b={b}" for (n, d), (c, p, b) in EST_PARAMS.items())
     return ("Chung-Lu exponent 2.1 + Hawkes (n=0.5, Exp 60 s), N=100,000, M=10,000,000, 2 years; "
             "motifs cycle/out-star/ping-pong x delta {600, 3600, 86400}; exact + estimate "
             f"({est}); graph ingest + adjacency build + one batched launch per step")
@@ -134,7 +141,7 @@ def make_queries(tm):
             meta.append((n, d, "exact"))
     for i, n in enumerate(MOTIF_NAMES):
         for j, d in enumerate(DELTAS):
-            c, p, b = EST_PARAMS[d]
+            c, p, b = EST_PARAMS[(n, d)]
             qs.append(tm.estimate_query(motifs[n], d, c, p, seed=1000 + 10 * i + j, b=b))
             meta.append((n, d, "estimate"))
     return motifs, qs, meta
@@ -142,6 +149,7 @@ def make_queries(tm):
 
 # ----------------------------------------------------------- calibration ---
 def calibrate(tm, g, motifs, exact, seeds=64, target=0.05, q=0.95):
+    target = float(os.environ.get("TM_CAL_TARGET", target))
     """For every (motif, delta): the cheapest (c, p, b) -- by b*p -- whose
     relative error |Z - C|/C stays within `target` for a fraction q of
     `seeds` independent seeds.  Prints one JSON line per (motif, delta)."""
@@ -190,7 +198,7 @@ def cpu_baseline(src, dst, t, meta, frac=1 / 800, budget_s=25.0):
             el = time.perf_counter() - t0
             total_proj += fixed + max(el - fixed, 0.0) / frac
         else:
-            c, p, b = EST_PARAMS[d]
+            c, p, b = EST_PARAMS[(name, d)]
             cd = c * d
             s = orng.shift(1000, 0, cd)
             wins = oracle.windows_of_shift(int(tn.max()), cd, s)

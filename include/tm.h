@@ -207,6 +207,24 @@ int tm_run_batch(const tm_graph* g, const tm_query* queries, int32_t n_queries,
 int tm_count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, void* stream,
                            int64_t* count);
 
+/* ---- prepared batches (CUDA graph) ----------------------------------------------
+ * A fixed set of queries on one graph, prepared once and launched many times:
+ * plans and weight tables are built at creation, scratch is sized for the worst
+ * case (every window of every shift kept), and the launch sequence -- window
+ * partition, first-edge scan, second-edge ranges, persistent matcher, fold,
+ * result copy -- is captured in one CUDA graph whose replay needs no host
+ * synchronisation.  Results are identical to tm_run_batch on the same queries.
+ *   tm_batch_create   captures on a private stream; TM_ENOMEM if the worst-case
+ *                     scratch does not fit.  The graph and motifs must outlive it.
+ *   tm_batch_launch   enqueues one replay on `stream` (asynchronous).
+ *   tm_batch_results  waits for `stream`, then copies the last replay's results.
+ * One replay at a time per batch: replays on different streams share scratch. */
+typedef struct tm_batch tm_batch;
+int tm_batch_create(const tm_graph* g, const tm_query* queries, int32_t n_queries, tm_batch** out);
+int tm_batch_launch(tm_batch* b, void* stream);
+int tm_batch_results(tm_batch* b, void* stream, tm_result* results);
+void tm_batch_free(tm_batch* b);
+
 /* ---- tuning ----------------------------------------------------------------
  * Matcher launch parameters.  0 keeps the current value.  The autotuner
  * (tm_autotune) writes these after timing candidates on a graph. */

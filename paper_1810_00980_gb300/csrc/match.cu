@@ -63,6 +63,7 @@ struct MatchArgs {
     WinDev W;
     int64_t NW;
     int64_t F;
+    const int64_t* d_F;    // if set, the first-edge count is read here on the device
     const int32_t* fwin;   // [F] window of each first edge
     const int64_t* lo2;    // [F] start of its second-edge candidate range
     const int64_t* excl;   // [F] exclusive scan of the range lengths
@@ -428,9 +429,10 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict
     Acc acc;
     acc.win = -1;
     acc_zero(acc);
-    for (int64_t base = warp * 32; base < A.F; base += nwarps * 32) {
+    const int64_t F = A.d_F ? *A.d_F : A.F;
+    for (int64_t base = warp * 32; base < F; base += nwarps * 32) {
         int64_t f = base + lane;
-        bool valid = f < A.F;
+        bool valid = f < F;
         int64_t wi = -1;
         if (valid) {
             int64_t lo = 0, hi = A.NW;
@@ -614,6 +616,7 @@ __global__ void __launch_bounds__(256) k_match(MatchArgs A) {
     const GraphDev& G = A.G;
     int lane = threadIdx.x & 31;
     int64_t W2 = *A.d_W2;
+    const int64_t F = A.d_F ? *A.d_F : A.F;
     Acc acc;
     acc.win = -1;
     acc_zero(acc);
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(256) k_match(MatchArgs A) {
         int64_t fb = 0, fe = 0;
         if (lane < 2) {
             int64_t key = lane == 0 ? c0 : c1 - 1;
-            fb = upper_bound_i64(A.excl, 0, A.F, key) - 1;
+            fb = upper_bound_i64(A.excl, 0, F, key) - 1;
         }
         fe = __shfl_sync(kFull, fb, 1);
         fb = __shfl_sync(kFull, fb, 0);
@@ -1033,7 +1036,7 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
             int64_t* hs_a = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             int64_t* hs_hi = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             MatchArgs A;
-            A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = F;
+            A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = F; A.d_F = nullptr;
             A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
             A.d_W2 = dW2; A.counter = dctr;
             A.enum_threshold = tu.enum_threshold;
@@ -1292,7 +1295,7 @@ int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cud
     if (F > 0) {
         const Tuning tu = tuning();
         MatchArgs A;
-        A.G = G; A.plans = dplan; A.nq = 1; A.W = W; A.NW = 1; A.F = F;
+        A.G = G; A.plans = dplan; A.nq = 1; A.W = W; A.NW = 1; A.F = F; A.d_F = nullptr;
         A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
         A.hs_a = nullptr; A.hs_hi = nullptr;
         A.enum_threshold = tu.enum_threshold;
@@ -1332,3 +1335,235 @@ extern "C" int tm_count_exact_noalloc(const tm_graph* g, const tm_motif* m, int6
                                       int64_t* count) {
     return tmo::count_exact_noalloc(g, m, delta, (cudaStream_t)stream, count);
 }
+
+// ---------------------------------------------------------------------------
+// Prepared batches: the run_batch launch sequence captured once in a CUDA
+// graph, with every size read on the device (first-edge count, candidate
+// count) and scratch sized for the worst case, so a replay never waits on the
+// host.
+// ---------------------------------------------------------------------------
+struct tm_batch {
+    const tm_graph* g = nullptr;
+    int nq = 0;
+    std::vector<int> qstat;
+    int first_err = TM_OK;
+    void* scratch = nullptr;
+    tm_result* h_res = nullptr;       // pinned: the graph's last node copies results here
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n_kernels = 0;
+};
+
+namespace tmo {
+namespace {
+
+void batch_release(tm_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) {
+        cudaStreamSynchronize(b->cap);
+        cudaStreamDestroy(b->cap);
+    }
+    if (b->scratch) cudaFree(b->scratch);
+    if (b->h_res) cudaFreeHost(b->h_res);
+    delete b;
+}
+
+int batch_create(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out) {
+    if (!out) { set_error("out is NULL"); return TM_EINVAL; }
+    *out = nullptr;
+    if (!g || !qs || nq <= 0) { set_error("bad argument"); return TM_EINVAL; }
+    tm_batch* b = new (std::nothrow) tm_batch();
+    if (!b) { set_error("host allocation failed"); return TM_ENOMEM; }
+    b->g = g;
+    b->nq = nq;
+    b->qstat.assign((size_t)nq, TM_OK);
+    std::vector<QPlan> hp((size_t)nq);
+    int64_t NW = 0, Fmax = 0;
+    int lmax = 1, kmax = 2;
+    bool any_hoist = false;
+    size_t wtab_bytes = 0;
+    for (int i = 0; i < nq; i++) {
+        std::string why;
+        int s = validate_query(g, qs[i], why);
+        QPlan& P = hp[(size_t)i];
+        if (s != TM_OK) {
+            b->qstat[(size_t)i] = s;
+            if (b->first_err == TM_OK) { b->first_err = s; set_error("query " + std::to_string(i) + ": " + why); }
+            std::memset(&P, 0, sizeof(QPlan));
+            P.win_base = NW;
+            continue;
+        }
+        fill_plan(P, qs[i], g);
+        P.win_base = NW;
+        NW += P.mode == TM_MODE_EXACT ? 1 : P.J * P.b;
+        Fmax += P.mode == TM_MODE_EXACT ? g->m : (int64_t)P.b * g->m;
+        lmax = std::max(lmax, P.l);
+        kmax = std::max(kmax, P.k);
+        any_hoist |= P.hoist != 0;
+        if (P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) wtab_bytes += a256(16 * (size_t)(P.delta + 1));
+    }
+    size_t NWs = (size_t)std::max<int64_t>(NW, 1), Fs = (size_t)std::max<int64_t>(Fmax, 1);
+    int64_t ws1 = 2 * ((NW + 2047) / 2048) + 2;
+    int64_t ws2 = scan_dn_ws_elems(Fmax) + 2;
+    size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
+                7 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
+                a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2);
+    cudaError_t e = cudaMalloc(&b->scratch, sz);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_res, sizeof(tm_result) * (size_t)nq);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        int rc = cuda_status(e, "tm_batch_create", __FILE__, __LINE__);
+        batch_release(b);
+        return rc;
+    }
+    char* p = (char*)b->scratch;
+    auto take = [&](size_t bytes) { char* r = p; p += a256(bytes); return (void*)r; };
+    QPlan* dplans = (QPlan*)take(sizeof(QPlan) * (size_t)nq);
+    tm_result* dres = (tm_result*)take(sizeof(tm_result) * (size_t)nq);
+    for (int i = 0; i < nq; i++) {
+        QPlan& P = hp[(size_t)i];
+        if (P.l > 0 && P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax)
+            P.wtab = (const uint64_t*)take(16 * (size_t)(P.delta + 1));
+    }
+    WinDev W;
+    W.lo = (int64_t*)take(8 * NWs);
+    W.hi = (int64_t*)take(8 * NWs);
+    W.tend = (int64_t*)take(8 * NWs);
+    W.start = (int64_t*)take(8 * NWs);
+    W.j = (int64_t*)take(8 * NWs);
+    W.nfirst = (int64_t*)take(8 * NWs);
+    W.fbase = (int64_t*)take(8 * NWs);
+    W.q = (int32_t*)take(4 * NWs);
+    W.k = (int32_t*)take(4 * NWs);
+    W.kept = (int32_t*)take(4 * NWs);
+    W.qj = (double*)take(8 * NWs);
+    W.acc = (unsigned long long*)take(8 * A_N * NWs);
+    int64_t* dF = (int64_t*)take(8);
+    int64_t* dW2 = (int64_t*)take(8);
+    unsigned long long* dctr = (unsigned long long*)take(8);
+    int32_t* fwin = (int32_t*)take(4 * Fs);
+    int64_t* lo2 = (int64_t*)take(8 * Fs);
+    int64_t* excl = (int64_t*)take(8 * Fs);
+    int64_t* hs_a = any_hoist ? (int64_t*)take(8 * Fs) : nullptr;
+    int64_t* hs_hi = any_hoist ? (int64_t*)take(8 * Fs) : nullptr;
+    int64_t* wsp1 = (int64_t*)take(8 * (size_t)ws1);
+    int64_t* wsp2 = (int64_t*)take(8 * (size_t)ws2);
+
+    cudaStream_t st = b->cap;
+    int rc = TM_OK;
+    auto fail = [&](cudaError_t ee, const char* what) {
+        if (rc == TM_OK && ee != cudaSuccess) rc = cuda_status(ee, what, __FILE__, __LINE__);
+    };
+    // once: plans and weight tables
+    fail(cudaMemcpyAsync(dplans, hp.data(), sizeof(QPlan) * (size_t)nq, cudaMemcpyHostToDevice, st), "plans");
+    for (int i = 0; i < nq && rc == TM_OK; i++) {
+        const QPlan& P = hp[(size_t)i];
+        if (P.wtab) {
+            int64_t n = P.delta + 1;
+            k_wtab<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>((uint64_t*)P.wtab, P.delta, P.cd);
+            count_launch();
+            fail(cudaGetLastError(), "k_wtab");
+        }
+    }
+    fail(cudaStreamSynchronize(st), "batch setup");
+    if (rc != TM_OK) { batch_release(b); return rc; }
+
+    // captured sequence
+    const Tuning tu = tuning();
+    int nsm = sm_count();
+    GraphDev G = g->dev;
+    tm_profile pr0;
+    tm_profile_last(&pr0);
+    fail(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    fail(cudaMemsetAsync(W.acc, 0, 8 * A_N * NWs, st), "acc");
+    fail(cudaMemsetAsync(dctr, 0, 8, st), "counter");
+    if (rc == TM_OK && NW > 0) {
+        unsigned gr = (unsigned)std::min<int64_t>((NW + 255) / 256, (int64_t)nsm * 16);
+        k_windows<<<gr, 256, 0, st>>>(G, dplans, nq, W, NW); count_launch();
+        fail(cudaGetLastError(), "k_windows");
+    }
+    if (rc == TM_OK) rc = scan_exclusive_i64_ws(W.nfirst, W.fbase, NW, dF, wsp1, ws1, st);
+    if (rc == TM_OK && Fmax > 0) {
+        MatchArgs A;
+        A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = Fmax; A.d_F = dF;
+        A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
+        A.d_W2 = dW2; A.counter = dctr;
+        A.enum_threshold = tu.enum_threshold;
+        A.chunk = tu.chunk_items;
+        int64_t gl2 = std::min<int64_t>((Fmax + 255) / 256, (int64_t)nsm * 8);
+        k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
+        fail(cudaGetLastError(), "k_level2");
+        if (rc == TM_OK) rc = scan_exclusive_i64_dn(excl, excl, Fmax, dF, dW2, wsp2, ws2, st);
+        if (rc == TM_OK) {
+            unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
+            int bt = tu.block_threads;
+            if (lmax <= 3 && kmax <= 4) k_match<3, 4><<<gm, bt, 0, st>>>(A);
+            else if (lmax <= 4 && kmax <= 4) k_match<4, 4><<<gm, bt, 0, st>>>(A);
+            else if (lmax <= 4) k_match<4, TM_K_MAX><<<gm, bt, 0, st>>>(A);
+            else k_match<TM_L_MAX, TM_K_MAX><<<gm, bt, 0, st>>>(A);
+            count_launch();
+            fail(cudaGetLastError(), "k_match");
+        }
+    }
+    if (rc == TM_OK) {
+        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres); count_launch();
+        fail(cudaGetLastError(), "k_fold");
+    }
+    fail(cudaMemcpyAsync(b->h_res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(st, &graph);
+    fail(ee, "end capture");
+    b->graph = graph;
+    if (rc == TM_OK) fail(cudaGraphInstantiate(&b->exec, graph, 0), "instantiate");
+    tm_profile pr1;
+    tm_profile_last(&pr1);
+    b->n_kernels = (int)(pr1.launches - pr0.launches);
+    count_launch(-b->n_kernels);   // capture launched nothing; replays are counted
+    if (rc != TM_OK) {
+        cudaGetLastError();
+        batch_release(b);
+        return rc;
+    }
+    *out = b;
+    return TM_OK;
+}
+
+}  // namespace
+}  // namespace tmo
+
+extern "C" {
+
+int tm_batch_create(const tm_graph* g, const tm_query* queries, int32_t n_queries, tm_batch** out) {
+    return tmo::batch_create(g, queries, n_queries, out);
+}
+
+int tm_batch_launch(tm_batch* b, void* stream) {
+    if (!b || !b->exec) { tmo::set_error("bad batch"); return TM_EINVAL; }
+    TM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    tmo::count_launch(b->n_kernels);
+    return TM_OK;
+}
+
+int tm_batch_results(tm_batch* b, void* stream, tm_result* results) {
+    if (!b || !results) { tmo::set_error("bad argument"); return TM_EINVAL; }
+    TM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int first = b->first_err;
+    for (int i = 0; i < b->nq; i++) {
+        results[i] = b->h_res[i];
+        if (b->qstat[(size_t)i] != TM_OK) {
+            std::memset(&results[i], 0, sizeof(tm_result));
+            results[i].status = b->qstat[(size_t)i];
+        } else if (results[i].status != TM_OK && first == TM_OK) {
+            first = results[i].status;
+            tmo::set_error("query " + std::to_string(i) + ": count or weight sum overflowed 2^63");
+        }
+    }
+    return first;
+}
+
+void tm_batch_free(tm_batch* b) { tmo::batch_release(b); }
+
+}  // extern "C"

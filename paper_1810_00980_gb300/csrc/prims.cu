@@ -103,6 +103,72 @@ __global__ void k_scan_small(const int64_t* in, int64_t* out, int64_t n, int64_t
 
 __global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
 
+// the same scans for an element count held in device memory (*d_n <= n_max);
+// tiles past *d_n contribute nothing and write nothing
+__global__ void k_scan_tiles_dn(const int64_t* in, int64_t* out, const int64_t* __restrict__ d_n,
+                                int64_t* __restrict__ sums) {
+    __shared__ int64_t smem[33];
+    int64_t n = *d_n;
+    if ((int64_t)blockIdx.x * kScanTile >= n) {
+        if (threadIdx.x == 0) sums[blockIdx.x] = 0;
+        return;
+    }
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        loc += v[i];
+    }
+    int64_t total;
+    int64_t run = block_excl_scan(loc, smem, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add_dn(int64_t* __restrict__ out, const int64_t* __restrict__ d_n,
+                              const int64_t* __restrict__ offs) {
+    int64_t n = *d_n;
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base >= n) return;
+    int64_t add = offs[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] += add;
+    }
+}
+
+__global__ void k_scan_small_dn(const int64_t* in, int64_t* out, const int64_t* __restrict__ d_n,
+                                int64_t* __restrict__ d_total) {
+    __shared__ int64_t smem[33];
+    int64_t n = *d_n;
+    int64_t base = (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        loc += v[i];
+    }
+    int64_t total;
+    int64_t run = block_excl_scan(loc, smem, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = total;
+}
+
 // ------------------------------------------------------------------ radix sort
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -244,6 +310,40 @@ int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d
     k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, n, sums); count_launch();
     k_scan_small<<<1, kScanThreads, 0, st>>>(sums, soffs, ntiles, d_total); count_launch();
     k_scan_add<<<(unsigned)ntiles, kScanThreads, 0, st>>>(out, n, soffs); count_launch();
+    TM_CUDA(cudaGetLastError());
+    return TM_OK;
+}
+
+int64_t scan_dn_ws_elems(int64_t n_max) {
+    if (n_max <= kScanTile) return 0;
+    int64_t ntiles = (n_max + kScanTile - 1) / kScanTile;
+    return 2 * ntiles + 2 * ((ntiles + kScanTile - 1) / kScanTile) + 2;
+}
+
+int scan_exclusive_i64_dn(const int64_t* in, int64_t* out, int64_t n_max, const int64_t* d_n,
+                          int64_t* d_total, int64_t* ws, int64_t ws_elems, cudaStream_t st) {
+    if (n_max <= 0) {
+        if (d_total) {
+            k_set_i64<<<1, 1, 0, st>>>(d_total, 0); count_launch();
+            TM_CUDA(cudaGetLastError());
+        }
+        return TM_OK;
+    }
+    if (n_max <= kScanTile) {
+        k_scan_small_dn<<<1, kScanThreads, 0, st>>>(in, out, d_n, d_total); count_launch();
+        TM_CUDA(cudaGetLastError());
+        return TM_OK;
+    }
+    int64_t ntiles = (n_max + kScanTile - 1) / kScanTile;
+    if (ws_elems < scan_dn_ws_elems(n_max)) return TM_EINVAL;
+    int64_t* sums = ws;
+    int64_t* soffs = ws + ntiles;
+    int64_t* inner = ws + 2 * ntiles;
+    k_scan_tiles_dn<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, d_n, sums); count_launch();
+    TM_CUDA(cudaGetLastError());
+    int rc = scan_exclusive_i64_ws(sums, soffs, ntiles, d_total, inner, ws_elems - 2 * ntiles, st);
+    if (rc != TM_OK) return rc;
+    k_scan_add_dn<<<(unsigned)ntiles, kScanThreads, 0, st>>>(out, d_n, soffs); count_launch();
     TM_CUDA(cudaGetLastError());
     return TM_OK;
 }

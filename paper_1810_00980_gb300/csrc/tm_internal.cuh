@@ -156,6 +156,12 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_
 int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,
                           int64_t* ws, int64_t ws_elems, cudaStream_t st);
 
+// exclusive scan of the first *d_n (<= n_max) elements, the count read on the
+// device; workspace of scan_dn_ws_elems(n_max) int64 (no allocation, capturable)
+int64_t scan_dn_ws_elems(int64_t n_max);
+int scan_exclusive_i64_dn(const int64_t* in, int64_t* out, int64_t n_max, const int64_t* d_n,
+                          int64_t* d_total, int64_t* ws, int64_t ws_elems, cudaStream_t st);
+
 int sm_count();
 // device memory pool (prims.cu): raise the default pool's release threshold once
 // per device; pool_free returns a stream-ordered block on an internal stream

@@ -93,6 +93,10 @@ _SIGS = {
     "tm_estimate_windows": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i32, _c_dbl, _c_u64, _c_i32, _c_i32,
                                            _vp, _c_i64, _vp, _vp]),
     "tm_run_batch": (ctypes.c_int, [_vp, _vp, _c_i32, _vp, _vp]),
+    "tm_batch_create": (ctypes.c_int, [_vp, _vp, _c_i32, _vp]),
+    "tm_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "tm_batch_results": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tm_batch_free": (None, [_vp]),
     "tm_get_tuning": (ctypes.c_int, [_vp]),
     "tm_set_tuning": (ctypes.c_int, [_vp]),
     "tm_autotune": (ctypes.c_int, [_vp, _vp, _c_i32, _vp]),
@@ -326,6 +330,41 @@ class Batch:
 
     def results(self):
         return [_result_dict(self.rarr[i]) for i in range(self.n)]
+
+
+class PreparedBatch:
+    """tm_batch_*: queries prepared once and replayed as one CUDA graph."""
+
+    def __init__(self, g: Graph, queries):
+        self.g = g
+        self.queries = list(queries)
+        self.n = len(self.queries)
+        self.qarr = (QueryC * max(self.n, 1))(*[q.to_c() for q in self.queries])
+        self.rarr = (ResultC * max(self.n, 1))()
+        h = _vp()
+        _check(lib().tm_batch_create(g.handle, ctypes.cast(self.qarr, _vp), self.n, ctypes.byref(h)),
+               "tm_batch_create")
+        self.handle = h.value
+
+    def launch(self, stream=None):
+        _check(lib().tm_batch_launch(self.handle, 0 if stream is None else int(stream)), "tm_batch_launch")
+
+    def results(self, stream=None, check: bool = True):
+        s = lib().tm_batch_results(self.handle, 0 if stream is None else int(stream), ctypes.cast(self.rarr, _vp))
+        if check:
+            _check(s, "tm_batch_results")
+        return [_result_dict(self.rarr[i]) for i in range(self.n)]
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().tm_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def run_batch(g: Graph, queries, stream=None, check: bool = True):

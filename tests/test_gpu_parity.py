@@ -316,3 +316,40 @@ def test_config2_full_size_sampled_windows(tm, orc):
     want = orc.count_exact(src, dst, t, ms, md, 600, threads=16)
     res = tm.run_batch(g, [tm.exact_query(tm.Motif(ms, md), 600)])[0]
     assert res["count"] == want
+
+
+def test_prepared_batch_cuda_graph_matches_run_batch(tm, orc):
+    """The captured CUDA graph of a batch gives the same results as tm_run_batch,
+    replay after replay (scratch re-zeroed inside the graph)."""
+    import torch
+    src, dst, t = synth.chung_lu_hawkes(2000, 150_000, 2.1, seed=25, horizon=4_000_000)
+    g = _graph(tm, src, dst, t)
+    qs = []
+    for n in ("cycle3", "outstar3", "pingpong", "cycle4"):
+        mo = tm.Motif(*synth.MOTIFS[n])
+        qs += [tm.exact_query(mo, 3600), tm.estimate_query(mo, 3600, 10, 0.3, 5, b=2),
+               tm.estimate_query(mo, 600, 5, 20.0, 6, q_mode=tm.TM_Q_EDGES)]
+    qs.append(tm.Query(tm.Motif([0, 1], [1, 0]), -5))         # rejected: its status only
+    want = tm.run_batch(g, qs, check=False)
+    pb = tm.PreparedBatch(g, qs)
+    st = torch.cuda.Stream()
+    for rep in range(3):
+        pb.launch(st.cuda_stream)
+        got = pb.results(st.cuda_stream, check=False)
+        for a, b in zip(got, want):
+            assert a == b
+    assert want[-1]["status"] == tm.TM_EINVAL
+    assert want[0]["count"] == orc.count_exact(src, dst, t, *synth.MOTIFS["cycle3"], 3600, threads=8)
+    pb.free()
+
+
+def test_autotune_keeps_results(tm):
+    src, dst, t = synth.chung_lu_hawkes(2000, 100_000, 2.1, seed=26, horizon=3_000_000)
+    g = _graph(tm, src, dst, t)
+    qs = [tm.exact_query(tm.Motif(*synth.MOTIFS[n]), 3600) for n in ("cycle3", "outstar3", "cycle4")]
+    before = [r["count"] for r in tm.run_batch(g, qs)]
+    best = tm.autotune(g, qs)
+    assert best["block_threads"] in (128, 256) and best["chunk_items"] % 32 == 0
+    assert tm.get_tuning() == best
+    assert [r["count"] for r in tm.run_batch(g, qs)] == before
+    tm.set_tuning(block_threads=256, blocks_per_sm=4, chunk_items=256, enum_threshold=48)
