@@ -147,6 +147,103 @@ def make_queries(tm):
     return motifs, qs, meta
 
 
+# --------------------------------------------------------------- serving ---
+SERVE_MOTIFS = ("cycle3", "outstar3", "pingpong", "cycle4")
+
+
+def serve_mix(tm, motifs, gids, rng, n):
+    """Config-4 style query stream: graph, motif, delta, exact or estimate
+    (c in {10, 30}, p in {0.01, 0.05, 0.1}) and seed drawn uniformly."""
+    qs = []
+    for _ in range(n):
+        gi = gids[int(rng.integers(len(gids)))]
+        mo = motifs[SERVE_MOTIFS[int(rng.integers(len(SERVE_MOTIFS)))]]
+        d = int(rng.choice([600, 3600, 86400]))
+        if rng.random() < 0.5:
+            qs.append((gi, tm.exact_query(mo, d)))
+        else:
+            qs.append((gi, tm.estimate_query(mo, d, int(rng.choice([10, 30])), float(rng.choice([0.01, 0.05, 0.1])),
+                                             int(rng.integers(1 << 40)))))
+    return qs
+
+
+def serve_bench(tm, graphs, rates, seconds=3.0, seed=7):
+    """Poisson arrivals at each rate for `seconds`; latency = submit -> result on
+    the host.  Returns per-rate throughput and p50/p99 latency, and the
+    one-query-per-launch plain exact counter's rate on the exact queries."""
+    from paper_1810_00980_gb300 import synth
+    motifs = {n: tm.Motif(*synth.MOTIFS[n]) for n in SERVE_MOTIFS}
+    out = []
+    rng = np.random.default_rng(seed)
+    with tm.Server(n_streams=2, max_batch=64, mem_budget_bytes=64 << 30) as srv:
+        gids = [srv.attach(g) for g in graphs]
+        # warm-up
+        for gi, q in serve_mix(tm, motifs, gids, rng, 16):
+            srv.wait(srv.submit(gi, q), 600_000)
+        for lam in rates:
+            n = max(8, int(lam * seconds))
+            qs = serve_mix(tm, motifs, gids, rng, n)
+            gaps = rng.exponential(1.0 / lam, n)
+            pending, lat, early = {}, [], {}
+            lock = threading.Lock()
+            state = {"stop": False, "done_t": 0.0}
+
+            def collector():
+                got = 0
+                while got < n:
+                    x = srv.wait_any(200)
+                    if x is None:
+                        continue
+                    now = time.perf_counter()
+                    with lock:
+                        t_sub = pending.pop(x[0], None)
+                    if t_sub is None:      # finished before the submitter recorded it
+                        with lock:
+                            early[x[0]] = now
+                        got += 1
+                        continue
+                    lat.append(now - t_sub)
+                    state["done_t"] = max(state["done_t"], now)
+                    got += 1
+
+            th = threading.Thread(target=collector, daemon=True)
+            th.start()
+            t0 = time.perf_counter()
+            nxt = t0
+            for (gi, q), gap in zip(qs, gaps):
+                nxt += gap
+                while True:
+                    now = time.perf_counter()
+                    if now >= nxt:
+                        break
+                    time.sleep(min(nxt - now, 0.002))
+                ts = time.perf_counter()
+                tk = srv.submit(gi, q)
+                with lock:
+                    if tk in early:       # completed before we stored its submit time
+                        now = early.pop(tk)
+                        lat.append(now - ts)
+                        state["done_t"] = max(state["done_t"], now)
+                    else:
+                        pending[tk] = ts
+            th.join()
+            done_t = state["done_t"]
+            el = done_t - t0
+            out.append({"offered_qps": lam, "queries": n, "achieved_qps": n / el,
+                        "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))})
+    # one query per launch, plain exact kernel, same kind of exact queries
+    ex = [(gi, q) for gi, q in serve_mix(tm, motifs, list(range(len(graphs))), np.random.default_rng(seed + 1), 40)
+          if q.mode == tm.TM_MODE_EXACT][:12]
+    t0 = time.perf_counter()
+    for gi, q in ex:
+        tm.count_exact_plain(graphs[gi], q.motif, q.delta)
+    plain = len(ex) / (time.perf_counter() - t0)
+    return {"graphs_edges": [int(g.info().m) for g in graphs], "rates": out,
+            "plain_one_query_per_launch_exact_qps": plain,
+            "mix": "graph x {cycle3, outstar3, pingpong, cycle4} x delta {600, 3600, 86400}; "
+                   "1/2 exact, 1/2 estimate c in {10, 30}, p in {0.01, 0.05, 0.1}; Poisson arrivals"}
+
+
 # ----------------------------------------------------------- calibration ---
 def calibrate(tm, g, motifs, exact, seeds=64, target=0.05, q=0.95):
     target = float(os.environ.get("TM_CAL_TARGET", target))
@@ -251,6 +348,89 @@ def run_reference(args, rank):
     print(json.dumps(out))
 
 
+def run_config3(args, tm, torch, world, rank):
+    """Batched estimator workload: Chung-Lu (exponent 2.0) + Hawkes, N = 1e6,
+    M = 1e8; the 4-cycle a->b->c->d->a at delta = 3,600 s; c in {10, 30, 100} x
+    p in {0.01, 0.1} x 32 seeds = 192 estimate queries in one batched launch per
+    step (after the graph ingest and adjacency build).  Errors against the
+    exact count, per (c, p): mean over seeds and the error of the 32-seed mean."""
+    from paper_1810_00980_gb300 import synth
+    src, dst, t = synth.config3_graph()
+    M = len(t)
+    d_src, d_dst, d_t = (torch.from_numpy(x).cuda() for x in (src, dst, t))
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    m4 = tm.Motif(*synth.MOTIFS["cycle4"])
+    tm.profile_enable(True)
+    g0 = tm.Graph(d_src, d_dst, d_t, stream=sh)
+    C = tm.run_batch(g0, [tm.exact_query(m4, 3600)], stream=sh)[0]["count"]
+    exact_ms = tm.profile_last()["batch_ms"]
+    combos = [(c, p) for c in (10, 30, 100) for p in (0.01, 0.1)]
+    qs = [tm.estimate_query(m4, 3600, c, p, seed=9000 + s) for (c, p) in combos for s in range(32)]
+    res0 = tm.run_batch(g0, qs, stream=sh)
+    errs = {}
+    for i, (c, p) in enumerate(combos):
+        zs = np.array([r["estimate"] for r in res0[32 * i: 32 * (i + 1)]])
+        errs[f"c={c},p={p}"] = {"mean_abs_rel_err": float(np.mean(np.abs(zs - C)) / C) if C else None,
+                                "rel_err_of_seed_mean": float(abs(zs.mean() - C) / C) if C else None}
+    g0.free()
+
+    def step():
+        with torch.cuda.stream(stream):
+            g = tm.Graph(d_src, d_dst, d_t, stream=sh)
+            b = tm.Batch(g, qs)
+            b.run(stream=sh)
+            g.free()
+        return b
+
+    for _ in range(args.warmup):
+        b = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    launches0 = tm.profile_last()["launches"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    match_ms = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            b = step()
+            match_ms.append(tm.profile_last()["match_ms"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    results = b.results()
+    launches = tm.profile_last()["launches"] - launches0
+    b_match = sum(12 * r["cand_edges"] + 16 * r["last_ranges"] + 8 * r["inst_read"] for r in results)
+    mm = statistics.median(match_ms)
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    achieved = b_match / (mm / 1e3) / 1e9 if mm > 0 else 0.0
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": world * len(qs) * args.steps / (total_ms / 1e3), "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "config 3: Chung-Lu exponent 2.0 + Hawkes, N=1,000,000, M=100,000,000, 2 years; "
+                               "4-cycle, delta=3600; c {10,30,100} x p {0.01,0.1} x 32 seeds = 192 estimate "
+                               "queries in one batched launch; graph ingest + adjacency build per step",
+                   "queries_per_step": len(qs), "edges": M, "l2": "inputs larger than L2"},
+        "exact_count": C, "exact_batch_ms": exact_ms, "errors": errs,
+        "first_edges_per_step": sum(r["first_edges"] for r in results),
+        "roofline": {"kernel": "k_match", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "algorithmic_bytes": b_match, "launch_ms": mm},
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -259,6 +439,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving run on four resident graphs of 1M, 10M, 25M and 50M edges")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--workload", default="config2", choices=["config2", "config3"])
     ap.add_argument("--calibrate", action="store_true",
                     help="print the cheapest estimator parameters meeting 5%% error, then exit")
     args = ap.parse_args()
@@ -280,6 +464,13 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_1810_00980_gb300 import tm
+
+    if args.workload == "config3":
+        run_config3(args, tm, torch, world, rank)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     src, dst, t = make_graph()
     M = len(t)
@@ -314,6 +505,11 @@ def main():
                 c = tm.count_exact_plain(g0, motifs[n], d)
                 assert c == exact[(n, d)], (n, d, c, exact[(n, d)])
         plain_qps = len(MOTIF_NAMES) * len(DELTAS) / (time.perf_counter() - t0)
+    g0.free()
+
+    # launch parameters picked by the library's autotuner on this batch (outside the timed region)
+    g0 = tm.Graph(d_src, d_dst, d_t, stream=sh)
+    tuned = tm.autotune(g0, qs)
     g0.free()
 
     batch = None
@@ -382,6 +578,27 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
 
+    # serving: continuous batching on resident graphs (outside the timed step)
+    serve = None
+    if not args.no_serve:
+        from paper_1810_00980_gb300 import synth
+        if args.serve_full:
+            sizes = (1_000_000, 10_000_000, 25_000_000, 50_000_000)
+        else:
+            sizes = (1_000_000, 10_000_000)
+        sgraphs = []
+        for i, m_e in enumerate(sizes):
+            if m_e == M:
+                s_, d_, t_ = src, dst, t
+            else:
+                s_, d_, t_ = synth.chung_lu_hawkes(max(10_000, m_e // 100), m_e, 2.1, seed=40 + i)
+            sgraphs.append(tm.Graph(torch.from_numpy(s_).cuda(), torch.from_numpy(d_).cuda(),
+                                    torch.from_numpy(t_).cuda()))
+        torch.cuda.synchronize()
+        serve = serve_bench(tm, sgraphs, rates=(20, 100, 400, 1600))
+        for gg in sgraphs:
+            gg.free()
+
     # roofline of the dominant kernel (the persistent matcher)
     pk = peaks()
     hbm = pk.get("hbm_gbs")
@@ -419,7 +636,7 @@ def main():
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": workload_desc(), "queries_per_step": nq, "edges": M,
                    "l2": "inputs larger than L2 (160 MB edge list; ~0.6 GB adjacency rebuilt every step)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "tuning": tuned},
         "edges_per_s": world * first_edges * args.steps / (total_ms / 1e3),
         "graph_edges_per_s": world * M * args.steps / (total_ms / 1e3),
         "instances_per_s": world * sum(r["count"] for r in results) * args.steps / (total_ms / 1e3),
@@ -433,6 +650,7 @@ def main():
         "cpu_baseline": cb,
         "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 16 * M,
                 "d2h_bytes_per_step": nq * ctypes.sizeof(tm.ResultC)},
+        "serve": serve,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

@@ -283,6 +283,10 @@ int tm_serve_poll(tm_server* s, uint64_t ticket, tm_result* r);
 /* Block until the ticket finishes (then as tm_serve_poll) or timeout_ms
  * passes (TM_ETIMEOUT; the ticket stays valid). */
 int tm_serve_wait(tm_server* s, uint64_t ticket, int64_t timeout_ms, tm_result* r);
+/* Block until any ticket finishes -- tickets come back in completion order --
+ * or timeout_ms passes (TM_ETIMEOUT).  Sets *ticket and *r, returns the
+ * ticket's final status and forgets it (as tm_serve_poll). */
+int tm_serve_wait_any(tm_server* s, int64_t timeout_ms, uint64_t* ticket, tm_result* r);
 /* Cancel a ticket that has not started: it finishes with TM_ECANCELLED.
  * TM_PENDING if it is already running or done. */
 int tm_serve_cancel(tm_server* s, uint64_t ticket);

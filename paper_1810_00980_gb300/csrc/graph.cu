@@ -113,18 +113,23 @@ __global__ void k_pair_index(const uint32_t* __restrict__ perm, const int32_t* _
     }
 }
 
-// Open-addressing hash of the static edges: key (src << 32 | dst) -> pair index.
-// Capacity is a power of two >= 2 P, so every probe chain ends at an empty slot.
+// Open-addressing hash of the static edges: key (src << 32 | dst) -> the pair's
+// time-sorted segment of pair_t, stored in the slot as (begin, length) so that a
+// lookup is one 16-byte load.  Capacity is a power of two >= 2 P, so every probe
+// chain ends at an empty slot.
 __global__ void k_hash_insert(const int32_t* __restrict__ pair_src, const int32_t* __restrict__ pair_dst,
-                              int64_t P, unsigned long long* __restrict__ slots, unsigned long long mask) {
+                              const int64_t* __restrict__ pair_off, int64_t P,
+                              unsigned long long* __restrict__ slots, unsigned long long mask) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long key = ((unsigned long long)(uint32_t)pair_src[p] << 32) | (uint32_t)pair_dst[p];
+        unsigned long long seg = ((unsigned long long)(uint32_t)(pair_off[p + 1] - pair_off[p]) << 32) |
+                                 (uint32_t)pair_off[p];
         unsigned long long h = sm64_mix(key) & mask;
         for (unsigned long long it = 0; it <= mask; it++) {
             unsigned long long prev = atomicCAS(&slots[2 * h], kHashEmpty, key);
             if (prev == kHashEmpty) {
-                slots[2 * h + 1] = (unsigned long long)p;
+                slots[2 * h + 1] = seg;
                 break;
             }
             h = (h + 1) & mask;
@@ -344,7 +349,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
             G.hmask = cap - 1;
             e = cudaMemsetAsync(g->hash_block, 0xff, 16 * cap, st);
             if (e == cudaSuccess) {
-                k_hash_insert<<<grid_for(P), kThreads, 0, st>>>((const int32_t*)kt, pair_dst, P,
+                k_hash_insert<<<grid_for(P), kThreads, 0, st>>>((const int32_t*)kt, pair_dst, pair_off, P,
                                                                (unsigned long long*)g->hash_block, cap - 1);
                 count_launch();
                 e = cudaGetLastError();

@@ -119,13 +119,13 @@ __device__ __forceinline__ bool pair_segment(const GraphDev& G, int32_t u, int32
     unsigned long long key = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
     unsigned long long h = sm64_mix(key) & G.hmask;
     for (unsigned long long it = 0; it <= G.hmask; it++) {
-        unsigned long long k = __ldg(G.hslots + 2 * h);
-        if (k == key) {
-            int64_t p = (int64_t)__ldg(G.hslots + 2 * h + 1);
-            a = __ldg(G.pair_off + p);
-            b = __ldg(G.pair_off + p + 1);
+        ulonglong2 sl = __ldg(reinterpret_cast<const ulonglong2*>(G.hslots) + h);
+        if (sl.x == key) {
+            a = (int64_t)(uint32_t)sl.y;
+            b = a + (int64_t)(sl.y >> 32);
             return true;
         }
+        unsigned long long k = sl.x;
         if (k == kHashEmpty) break;
         h = (h + 1) & G.hmask;
     }

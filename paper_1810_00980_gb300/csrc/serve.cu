@@ -37,6 +37,7 @@ struct tm_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
+    std::deque<uint64_t> done_q;     // finished tickets in completion order (for wait_any)
     std::unordered_map<uint64_t, Ticket> tickets;
     std::vector<std::thread> workers;
     int64_t in_use = 0;
@@ -85,6 +86,7 @@ void worker_main(tm_server* S) {
                             T.status = TM_EADMIT;
                             std::memset(&T.r, 0, sizeof(T.r));
                             T.r.status = TM_EADMIT;
+                            S->done_q.push_back(*it);
                             it = S->queue.erase(it);
                             S->cv_done.notify_all();
                             continue;
@@ -120,6 +122,7 @@ void worker_main(tm_server* S) {
                     T.r.status = rc;  // batch-level failure (CUDA, memory)
                 }
                 T.status = T.r.status;
+                S->done_q.push_back(ids[i]);
             }
         }
         S->cv_done.notify_all();
@@ -221,6 +224,27 @@ int tm_serve_wait(tm_server* S, uint64_t ticket, int64_t timeout_ms, tm_result* 
     }
 }
 
+int tm_serve_wait_any(tm_server* S, int64_t timeout_ms, uint64_t* ticket, tm_result* r) {
+    if (!S || !ticket || !r) { tmo::set_error("NULL argument"); return TM_EINVAL; }
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    for (;;) {
+        while (!S->done_q.empty()) {
+            uint64_t id = S->done_q.front();
+            S->done_q.pop_front();
+            auto it = S->tickets.find(id);
+            if (it == S->tickets.end() || it->second.state != kDone) continue;  // already collected
+            *ticket = id;
+            *r = it->second.r;
+            int st = it->second.status;
+            S->tickets.erase(it);
+            return st;
+        }
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && S->done_q.empty())
+            return TM_ETIMEOUT;
+    }
+}
+
 int tm_serve_cancel(tm_server* S, uint64_t ticket) {
     if (!S) { tmo::set_error("NULL argument"); return TM_EINVAL; }
     std::lock_guard<std::mutex> lk(S->mu);
@@ -233,6 +257,7 @@ int tm_serve_cancel(tm_server* S, uint64_t ticket) {
     it->second.status = TM_ECANCELLED;
     std::memset(&it->second.r, 0, sizeof(tm_result));
     it->second.r.status = TM_ECANCELLED;
+    S->done_q.push_back(ticket);
     S->cv_done.notify_all();
     return TM_OK;
 }

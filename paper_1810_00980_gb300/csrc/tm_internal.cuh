@@ -53,7 +53,7 @@ struct GraphDev {
     const int64_t* pair_t;  // [m]
     const int32_t* out_src; // [m] source of each out-view entry (the sort key)
     const int32_t* in_dst;  // [m] destination of each in-view entry
-    const unsigned long long* hslots;  // [2*(hmask+1)]: (key, pair index) per slot
+    const unsigned long long* hslots;  // [2*(hmask+1)]: key, then (length << 32 | begin) of the pair's segment
     unsigned long long hmask;          // hash capacity - 1 (power of two)
 };
 

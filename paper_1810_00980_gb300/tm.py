@@ -107,6 +107,7 @@ _SIGS = {
     "tm_serve_submit": (ctypes.c_int, [_vp, _c_i32, _vp, _vp]),
     "tm_serve_poll": (ctypes.c_int, [_vp, _c_u64, _vp]),
     "tm_serve_wait": (ctypes.c_int, [_vp, _c_u64, _c_i64, _vp]),
+    "tm_serve_wait_any": (ctypes.c_int, [_vp, _c_i64, _vp, _vp]),
     "tm_serve_cancel": (ctypes.c_int, [_vp, _c_u64]),
     "tm_serve_destroy": (None, [_vp]),
 }
@@ -442,6 +443,16 @@ class Server:
             return None
         self._pending.pop(ticket, None)
         return s, _result_dict(r)
+
+    def wait_any(self, timeout_ms: int = 60_000):
+        """Next finished ticket in completion order: (ticket, status, result), or None on timeout."""
+        r = ResultC()
+        t = _c_u64()
+        s = lib().tm_serve_wait_any(self.handle, int(timeout_ms), ctypes.byref(t), ctypes.byref(r))
+        if s == TM_ETIMEOUT:
+            return None
+        self._pending.pop(t.value, None)
+        return t.value, s, _result_dict(r)
 
     def cancel(self, ticket: int) -> int:
         return lib().tm_serve_cancel(self.handle, int(ticket))

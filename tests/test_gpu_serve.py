@@ -108,3 +108,18 @@ def test_shutdown_drains_queue(tm, graphs):
     srv.close()   # destroy: finishes queued work, then stops
     with pytest.raises(Exception):
         srv.submit(gid, tm.exact_query(mo, 600))
+
+
+def test_wait_any_returns_every_ticket_once(tm, graphs):
+    mo = tm.Motif(*synth.MOTIFS["outstar3"])
+    with tm.Server(n_streams=2, max_batch=8) as srv:
+        gid = srv.attach(graphs[0])
+        want = {srv.submit(gid, tm.estimate_query(mo, 3600, 10, 0.2, s)): s for s in range(30)}
+        seen = set()
+        while len(seen) < len(want):
+            x = srv.wait_any(120_000)
+            assert x is not None
+            tk, st, r = x
+            assert st == tm.TM_OK and tk in want and tk not in seen
+            seen.add(tk)
+        assert srv.wait_any(50) is None          # nothing left: times out
