@@ -537,6 +537,7 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
     const GraphDev& G = A.G;
     int lane = threadIdx.x & 31;
     int64_t lo = 0, len = 0;
+    int dir = 0;   // 1: this lane's candidates are the last edge's (two-sided closing)
     if (valid) {
         const QPlan& Q = A.plans[q];
         const LevelPlan P = Q.lv[D];
@@ -545,6 +546,28 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
             len = hh - lo;
         } else {
             level_range(G, P, phi, tprev, thi, lo, len);
+        }
+        if constexpr (D + 2 <= LMAX) {
+            if (D == Q.l - 2 && Q.rev2 && len > 0) {
+                // edge D binds one new node x and the last edge joins x to a bound
+                // node: take whichever side has fewer candidates in (tprev, thi]
+                const LevelPlan L = Q.lv[Q.l - 1];
+                int xl = P.bind_u ? P.su : P.sv;
+                bool x_src = L.su == xl;
+                int32_t bn = x_src ? phi_get(phi, L.sv) : phi_get(phi, L.su);
+                const int64_t* ta = x_src ? G.in_t : G.out_t;
+                const int64_t* off = x_src ? G.in_off : G.out_off;
+                int64_t a = __ldg(off + bn), b = __ldg(off + bn + 1);
+                int64_t rlo = upper_bound_i64(ta, a, b, tprev);
+                int64_t rlen = gallop_ub(ta, rlo, b, thi) - rlo;
+                if (rlen == 0) {
+                    len = 0;
+                } else if (rlen < len) {
+                    lo = rlo;
+                    len = rlen;
+                    dir = 1;
+                }
+            }
         }
         if (D == Q.l - 1) {
             acc_switch(acc, win, A.W.acc);
@@ -581,6 +604,12 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
         int64_t othi = __shfl_sync(kFull, thi, o);
         int64_t oha = __shfl_sync(kFull, ha, o);
         int64_t ohh = __shfl_sync(kFull, hh, o);
+        int odir = 0;
+        int64_t otp = 0;
+        if constexpr (D + 2 <= LMAX) {
+            odir = __shfl_sync(kFull, dir, o);
+            otp = __shfl_sync(kFull, tprev, o);
+        }
         int32_t ophi[KMAX];
 #pragma unroll
         for (int i = 0; i < KMAX; i++) ophi[i] = __shfl_sync(kFull, phi[i], o);
@@ -589,19 +618,49 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
         if (has) {
             const QPlan& Q = A.plans[oq];
             const LevelPlan P = Q.lv[D];
-            int32_t s, d;
-            read_cand(G, P, ophi, olo + (x - ost), s, d, tc);
-            ok = check_bind(P, ophi, s, d);
             acc_switch(acc, ow, A.W.acc);
-            if (D == Q.l - 1) {
-                acc.f[A_INST] += 1;
-                if (ok) {
-                    acc.f[A_COUNT] += 1;
-                    if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - ot1);
+            if (odir) {
+                // last-edge candidate (x, t_l): count the edge-D candidates in (tprev, t_l)
+                const LevelPlan L = Q.lv[Q.l - 1];
+                int xl = P.bind_u ? P.su : P.sv;
+                bool x_src = L.su == xl;
+                int64_t c = olo + (x - ost);
+                int32_t xv = x_src ? __ldg(G.in_nbr + c) : __ldg(G.out_nbr + c);
+                int64_t tl = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
+                acc.f[A_CAND] += 1;
+                if (!phi_has(ophi, P.nb, xv)) {
+                    int32_t mu = P.bind_u ? xv : phi_get(ophi, P.su);
+                    int32_t mv = P.bind_v ? xv : phi_get(ophi, P.sv);
+                    int64_t cnt = pair_count(G, mu, mv, otp, tl - 1);
+                    acc.f[A_LAST] += 1;
+                    if (cnt) {
+                        acc.f[A_COUNT] += cnt;
+                        if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, tl - ot1, (unsigned long long)cnt);
+                    }
                 }
             } else {
-                acc.f[A_CAND] += 1;
-                deeper = ok;
+                int32_t s, d;
+                read_cand(G, P, ophi, olo + (x - ost), s, d, tc);
+                ok = check_bind(P, ophi, s, d);
+                if (D == Q.l - 1) {
+                    acc.f[A_INST] += 1;
+                    if (ok) {
+                        acc.f[A_COUNT] += 1;
+                        if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - ot1);
+                    }
+                } else {
+                    acc.f[A_CAND] += 1;
+                    deeper = ok;
+                    if constexpr (D + 2 <= LMAX) {
+                        const LevelPlan L = Q.lv[Q.l - 1];
+                        if (ok && D == Q.l - 2 && Q.mode == TM_MODE_EXACT && L.view == kPair && !Q.hoist) {
+                            // close here: the last edge counted by range length
+                            acc.f[A_COUNT] += pair_count(G, phi_get(ophi, L.su), phi_get(ophi, L.sv), tc, othi);
+                            acc.f[A_LAST] += 1;
+                            deeper = false;
+                        }
+                    }
+                }
             }
         }
         if constexpr (D + 1 < LMAX) {
@@ -611,8 +670,9 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
     }
 }
 
+// three-edge motifs fit in 64 registers: ask for four resident 256-thread blocks per SM
 template <int LMAX, int KMAX>
-__global__ void __launch_bounds__(256) k_match(MatchArgs A) {
+__global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs A) {
     const GraphDev& G = A.G;
     int lane = threadIdx.x & 31;
     int64_t W2 = *A.d_W2;
@@ -893,6 +953,15 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
     if (m->l >= 3) {
         const LevelPlan& L = m->lv[m->l - 1];
         P.hoist = (L.view == kPair && L.su <= 1 && L.sv <= 1) ? 1 : 0;
+    }
+    P.rev2 = 0;
+    if (m->l >= 4) {
+        const LevelPlan& LD = m->lv[m->l - 2];
+        const LevelPlan& L = m->lv[m->l - 1];
+        bool one_new = (LD.view == kOut || LD.view == kIn) && (LD.bind_u + LD.bind_v == 1);
+        int xl = LD.bind_u ? LD.su : LD.sv;
+        bool closes_x = L.view == kPair && ((L.su == xl && L.sv < LD.nb) || (L.sv == xl && L.su < LD.nb));
+        P.rev2 = (one_new && closes_x) ? 1 : 0;
     }
     if (m->l == 3) {
         const LevelPlan& L1 = m->lv[1];

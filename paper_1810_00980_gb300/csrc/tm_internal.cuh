@@ -115,6 +115,8 @@ struct QPlan {
     int32_t rev;         // 1: three edges, the second binds one new node x and the last
                          //    joins x to a first-edge node: instances can be closed from
                          //    either the second or the last edge's candidates
+    int32_t rev2;        // 1: four or more edges, and the same holds for the last two
+    int32_t pad1;
     int64_t delta;
     int64_t cd;          // c * delta (estimate), 0 for exact
     int64_t J;           // windows per shift (estimate), 1 for exact
