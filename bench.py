@@ -443,6 +443,8 @@ def main():
                     help="serving run on four resident graphs of 1M, 10M, 25M and 50M edges")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--workload", default="config2", choices=["config2", "config3"])
+    ap.add_argument("--tuning", default="auto",
+                    help="'auto' (autotune on the batch) or block_threads,blocks_per_sm,chunk_items,enum_threshold")
     ap.add_argument("--calibrate", action="store_true",
                     help="print the cheapest estimator parameters meeting 5%% error, then exit")
     args = ap.parse_args()
@@ -508,9 +510,14 @@ def main():
     g0.free()
 
     # launch parameters picked by the library's autotuner on this batch (outside the timed region)
-    g0 = tm.Graph(d_src, d_dst, d_t, stream=sh)
-    tuned = tm.autotune(g0, qs)
-    g0.free()
+    if args.tuning == "auto":
+        g0 = tm.Graph(d_src, d_dst, d_t, stream=sh)
+        tuned = tm.autotune(g0, qs)
+        g0.free()
+    else:
+        bt, bps, ch, th = (int(x) for x in args.tuning.split(","))
+        tm.set_tuning(block_threads=bt, blocks_per_sm=bps, chunk_items=ch, enum_threshold=th)
+        tuned = tm.get_tuning()
 
     batch = None
 
@@ -530,7 +537,7 @@ def main():
     launches0 = tm.profile_last()["launches"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    match_ms, prof = [], []
+    match_ms, level2_ms, prof = [], [], []
     step_ms = []
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
@@ -544,6 +551,7 @@ def main():
             p = tm.profile_last()
             prof.append(p)
             match_ms.append(p["match_ms"])
+            level2_ms.append(p["level2_ms"])
             s1.synchronize()
             step_ms.append(s0.elapsed_time(s1))
         e1.record(stream)
@@ -599,18 +607,26 @@ def main():
         for gg in sgraphs:
             gg.free()
 
-    # roofline of the dominant kernel (the persistent matcher)
+    # roofline of the dominant kernel (the longer of k_level2 and k_match)
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
+    # algorithmic bytes: k_match reads each candidate (12 B), two boundary timestamps per
+    # range-counted closing (16 B) and each last-edge entry read one by one (8 B);
+    # k_level2 reads each first edge (16 B) and its range boundaries (16 B), and writes
+    # its per-first-edge record (window 4 B, range start 8 B, length 8 B)
     b_match = sum(12 * r["cand_edges"] + 16 * r["last_ranges"] + 8 * r["inst_read"] for r in results)
+    b_level2 = sum((16 + 16 + 20) * r["first_edges"] for r in results)
     mm = statistics.median(match_ms) if match_ms else float("nan")
-    achieved = b_match / (mm / 1e3) / 1e9 if mm and mm > 0 else 0.0
+    ml = statistics.median(level2_ms) if level2_ms else float("nan")
+    dominant = "k_level2" if ml > mm else "k_match"
+    kb, kms = (b_level2, ml) if dominant == "k_level2" else (b_match, mm)
+    achieved = kb / (kms / 1e3) / 1e9 if kms and kms > 0 else 0.0
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "k_match_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", f"{dominant}_traffic.json")
     if os.path.exists(tfile):
-        # counters are only valid for the kernel source they were taken on
+        # counters are only valid for the kernel source and workload they were taken on
         try:
             import hashlib
             tj = json.load(open(tfile))
@@ -620,6 +636,10 @@ def main():
                 traffic = tj.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
+    other = {"k_match": {"ms": mm, "algorithmic_bytes": b_match,
+                         "achieved_gbs": b_match / (mm / 1e3) / 1e9 if mm > 0 else 0.0},
+             "k_level2": {"ms": ml, "algorithmic_bytes": b_level2,
+                          "achieved_gbs": b_level2 / (ml / 1e3) / 1e9 if ml > 0 else 0.0}}
 
     if rank != 0:
         if world > 1:
@@ -644,9 +664,9 @@ def main():
         "plain_exact_queries_per_s": plain_qps,
         "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
         "phases_ms": {k: p_last.get(k) for k in ("graph_ms", "windows_ms", "level2_ms", "match_ms", "fold_ms")},
-        "roofline": {"kernel": "k_match", "bound": "hbm", "achieved": achieved, "peak": hbm,
+        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                     "algorithmic_bytes": b_match, "launch_ms": mm},
+                     "algorithmic_bytes": kb, "launch_ms": kms, "kernels": other},
         "cpu_baseline": cb,
         "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 16 * M,
                 "d2h_bytes_per_step": nq * ctypes.sizeof(tm.ResultC)},

@@ -249,7 +249,7 @@ int tm_autotune(const tm_graph* g, const tm_query* queries, int32_t n_queries, t
 typedef struct {
     double graph_ms;        /* last graph build: validation through the last view */
     double windows_ms;      /* last batch: weight tables + window partition + first-edge scan */
-    double level2_ms;       /* second-edge ranges of every first edge + their scan */
+    double level2_ms;       /* second-edge ranges of every first edge (k_level2) */
     double match_ms;        /* the persistent matcher launch */
     double fold_ms;         /* per-query combination */
     double batch_ms;        /* whole batch, first launch to results on the host */

@@ -41,9 +41,10 @@ __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __res
     if ((threadIdx.x & 31) == 0) atomicMax(&flags[2], mx);
 }
 
+template <typename TT>
 __global__ void k_ingest(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                          const int64_t* __restrict__ t, int64_t m, int64_t tmin,
-                         int32_t* __restrict__ gs, int32_t* __restrict__ gd, int64_t* __restrict__ gt,
+                         int32_t* __restrict__ gs, int32_t* __restrict__ gd, TT* __restrict__ gt,
                          uint32_t* __restrict__ key_src, uint32_t* __restrict__ key_dst,
                          uint32_t* __restrict__ iota_a, uint32_t* __restrict__ iota_b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
@@ -51,7 +52,7 @@ __global__ void k_ingest(const int32_t* __restrict__ src, const int32_t* __restr
         int32_t s = src[i], d = dst[i];
         gs[i] = s;
         gd[i] = d;
-        gt[i] = t[i] - tmin;
+        gt[i] = (TT)(t[i] - tmin);
         key_src[i] = (uint32_t)s;
         key_dst[i] = (uint32_t)d;
         iota_a[i] = (uint32_t)i;
@@ -71,9 +72,10 @@ __global__ void k_offsets(const uint32_t* __restrict__ keys, int64_t m, int32_t 
 }
 
 // out_nbr/out_t (or in_*) gathered through the sort permutation
+template <typename TT>
 __global__ void k_gather_view(const uint32_t* __restrict__ perm, const int32_t* __restrict__ other,
-                              const int64_t* __restrict__ t, int64_t m, int32_t* __restrict__ nbr,
-                              int64_t* __restrict__ tv) {
+                              const TT* __restrict__ t, int64_t m, int32_t* __restrict__ nbr,
+                              TT* __restrict__ tv) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t e = perm[i];
@@ -83,9 +85,10 @@ __global__ void k_gather_view(const uint32_t* __restrict__ perm, const int32_t* 
 }
 
 // pair view: positions sorted by (src, dst, time); head flag where the pair changes
+template <typename TT>
 __global__ void k_pair_heads(const uint32_t* __restrict__ perm, const int32_t* __restrict__ src,
-                             const int32_t* __restrict__ dst, const int64_t* __restrict__ t,
-                             int64_t m, int64_t* __restrict__ head, int64_t* __restrict__ pair_t) {
+                             const int32_t* __restrict__ dst, const TT* __restrict__ t,
+                             int64_t m, int64_t* __restrict__ head, TT* __restrict__ pair_t) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t e = perm[i];
@@ -206,11 +209,14 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
 
     // ---- one allocation for the resident graph
     size_t nN = (size_t)n + 1, M = (size_t)m;
+    // time arrays hold int32 when every normalised time fits, else int64
+    const int tb = tmax <= (int64_t)INT32_MAX ? 4 : 8;
     size_t sz_i32m = align256(4 * M), sz_i64m = align256(8 * M), sz_off = align256(8 * nN);
-    size_t total = 2 * sz_i32m + sz_i64m        // src, dst, t
-                 + sz_off + sz_i32m + sz_i64m   // out view
-                 + sz_off + sz_i32m + sz_i64m   // in view
-                 + sz_off + sz_i32m + align256(8 * (M + 1)) + sz_i64m   // pair view (P <= m)
+    size_t sz_tm = align256((size_t)tb * M);
+    size_t total = 2 * sz_i32m + sz_tm          // src, dst, t
+                 + sz_off + sz_i32m + sz_tm     // out view
+                 + sz_off + sz_i32m + sz_tm     // in view
+                 + sz_off + sz_i32m + align256(8 * (M + 1)) + sz_tm   // pair view (P <= m)
                  + 2 * sz_i32m;                                          // view keys
     tm_graph* g = new (std::nothrow) tm_graph();
     if (!g) { set_error("host allocation failed"); return TM_ENOMEM; }
@@ -230,22 +236,22 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     auto take = [&](size_t bytes) { char* r = p; p += bytes; return (void*)r; };
     int32_t* gs = (int32_t*)take(sz_i32m);
     int32_t* gd = (int32_t*)take(sz_i32m);
-    int64_t* gt = (int64_t*)take(sz_i64m);
+    void* gt = take(sz_tm);
     int64_t* out_off = (int64_t*)take(sz_off);
     int32_t* out_nbr = (int32_t*)take(sz_i32m);
-    int64_t* out_t = (int64_t*)take(sz_i64m);
+    void* out_t = take(sz_tm);
     int64_t* in_off = (int64_t*)take(sz_off);
     int32_t* in_nbr = (int32_t*)take(sz_i32m);
-    int64_t* in_t = (int64_t*)take(sz_i64m);
+    void* in_t = take(sz_tm);
     int64_t* pk_off = (int64_t*)take(sz_off);
     int32_t* pair_dst = (int32_t*)take(sz_i32m);
     int64_t* pair_off = (int64_t*)take(align256(8 * (M + 1)));
-    int64_t* pair_t = (int64_t*)take(sz_i64m);
+    void* pair_t = take(sz_tm);
     int32_t* out_src = (int32_t*)take(sz_i32m);
     int32_t* in_dst = (int32_t*)take(sz_i32m);
 
     GraphDev& G = g->dev;
-    G.m = m; G.n = n;
+    G.m = m; G.n = n; G.tbytes = tb;
     G.src = gs; G.dst = gd; G.t = gt;
     G.out_off = out_off; G.out_nbr = out_nbr; G.out_t = out_t;
     G.in_off = in_off; G.in_nbr = in_nbr; G.in_t = in_t;
@@ -293,13 +299,29 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
 
     int bits = bits_for(n);
     unsigned gr = grid_for(m);
-    k_ingest<<<gr, kThreads, 0, st>>>(d_src, d_dst, d_t, m, tmin, gs, gd, gt, ks, kd, va, vb); count_launch();
+    // the launches below that move timestamps, for the chosen element type
+    auto typed_launch = [&](auto tag, int which, const uint32_t* perm, const int32_t* other, int32_t* nbr,
+                            void* tv) {
+        using TT = decltype(tag);
+        if (which == 0)
+            k_ingest<TT><<<gr, kThreads, 0, st>>>(d_src, d_dst, d_t, m, tmin, gs, gd, (TT*)gt, ks, kd, va, vb);
+        else if (which == 1)
+            k_gather_view<TT><<<gr, kThreads, 0, st>>>(perm, other, (const TT*)gt, m, nbr, (TT*)tv);
+        else
+            k_pair_heads<TT><<<gr, kThreads, 0, st>>>(perm, gs, gd, (const TT*)gt, m, head, (TT*)tv);
+        count_launch();
+    };
+    auto tlaunch = [&](int which, const uint32_t* perm, const int32_t* other, int32_t* nbr, void* tv) {
+        if (tb == 4) typed_launch(int32_t{}, which, perm, other, nbr, tv);
+        else typed_launch(int64_t{}, which, perm, other, nbr, tv);
+    };
+    tlaunch(0, nullptr, nullptr, nullptr, nullptr);
     if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
     // out view: edges stably sorted by source (time order kept inside a source)
     if (rc == TM_OK) rc = radix_sort_pairs(ks, va, kt, vt, m, bits, st);
     if (rc == TM_OK) {
         k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(ks, m, n, out_off); count_launch();
-        k_gather_view<<<gr, kThreads, 0, st>>>(va, gd, gt, m, out_nbr, out_t); count_launch();
+        tlaunch(1, va, gd, out_nbr, out_t);
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
         if (rc == TM_OK && cudaMemcpyAsync(out_src, ks, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             rc = TM_ECUDA;
@@ -308,19 +330,19 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     if (rc == TM_OK) rc = radix_sort_pairs(kd, vb, kt, vt, m, bits, st);
     if (rc == TM_OK) {
         k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kd, m, n, in_off); count_launch();
-        k_gather_view<<<gr, kThreads, 0, st>>>(vb, gs, gt, m, in_nbr, in_t); count_launch();
+        tlaunch(1, vb, gs, in_nbr, in_t);
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
         if (rc == TM_OK && cudaMemcpyAsync(in_dst, kd, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             rc = TM_ECUDA;
     }
     // pair view: the in-view order stably re-sorted by source = (src, dst, time)
     if (rc == TM_OK) {
-        k_gather_view<<<gr, kThreads, 0, st>>>(vb, gs, gt, m, (int32_t*)ks, (int64_t*)head); count_launch();
+        tlaunch(1, vb, gs, (int32_t*)ks, head);   // sources in in-view order; times go to scratch
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
     }
     if (rc == TM_OK) rc = radix_sort_pairs(ks, vb, kt, vt, m, bits, st);
     if (rc == TM_OK) {
-        k_pair_heads<<<gr, kThreads, 0, st>>>(vb, gs, gd, gt, m, head, pair_t); count_launch();
+        tlaunch(2, vb, nullptr, nullptr, pair_t);
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
     }
     if (rc == TM_OK) rc = scan_exclusive_i64(head, pid, m, dP, st);

@@ -56,8 +56,9 @@ struct WinDev {
     unsigned long long* acc;  // [NW][A_N]
 };
 
+template <typename TT>
 struct MatchArgs {
-    GraphDev G;
+    GraphDevT<TT> G;
     const QPlan* plans;
     int nq;
     WinDev W;
@@ -100,10 +101,11 @@ __device__ __forceinline__ bool phi_has(const int32_t (&phi)[K], int nb, int32_t
 
 // first index in [lo, hi) with a[idx] > v, by exponential then binary search
 // from lo: about 2 log2(answer - lo) probes, cheap when the answer is near lo
-__device__ __forceinline__ int64_t gallop_ub(const int64_t* __restrict__ a, int64_t lo, int64_t hi,
+template <typename T>
+__device__ __forceinline__ int64_t gallop_ub(const T* __restrict__ a, int64_t lo, int64_t hi,
                                              int64_t v) {
     int64_t cur = lo, step = 1;
-    while (cur < hi && __ldg(a + cur) <= v) {
+    while (cur < hi && (int64_t)__ldg(a + cur) <= v) {
         lo = cur + 1;
         cur += step;
         step <<= 1;
@@ -114,7 +116,8 @@ __device__ __forceinline__ int64_t gallop_ub(const int64_t* __restrict__ a, int6
 
 // time-sorted entries of the (u -> v) pair: [a, b) of pair_t, through the
 // open-addressing hash of static edges (probe chains end at an empty slot)
-__device__ __forceinline__ bool pair_segment(const GraphDev& G, int32_t u, int32_t v, int64_t& a,
+template <typename TT>
+__device__ __forceinline__ bool pair_segment(const GraphDevT<TT>& G, int32_t u, int32_t v, int64_t& a,
                                              int64_t& b) {
     unsigned long long key = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
     unsigned long long h = sm64_mix(key) & G.hmask;
@@ -133,7 +136,8 @@ __device__ __forceinline__ bool pair_segment(const GraphDev& G, int32_t u, int32
     return false;
 }
 
-__device__ __forceinline__ int64_t pair_count(const GraphDev& G, int32_t u, int32_t v, int64_t tprev,
+template <typename TT>
+__device__ __forceinline__ int64_t pair_count(const GraphDevT<TT>& G, int32_t u, int32_t v, int64_t tprev,
                                               int64_t thi) {
     int64_t a, b;
     if (thi <= tprev || !pair_segment(G, u, v, a, b)) return 0;
@@ -144,11 +148,11 @@ __device__ __forceinline__ int64_t pair_count(const GraphDev& G, int32_t u, int3
 
 // candidates of motif edge P given the bound nodes: entries [lo, lo+len) of
 // the view's time array with time in (tprev, thi]
-template <int K>
-__device__ __forceinline__ void level_range(const GraphDev& G, const LevelPlan& P,
+template <typename TT, int K>
+__device__ __forceinline__ void level_range(const GraphDevT<TT>& G, const LevelPlan& P,
                                             const int32_t (&phi)[K], int64_t tprev, int64_t thi,
                                             int64_t& lo, int64_t& len) {
-    const int64_t* ta;
+    const TT* ta;
     int64_t a, b;
     lo = 0;
     len = 0;
@@ -170,8 +174,8 @@ __device__ __forceinline__ void level_range(const GraphDev& G, const LevelPlan& 
 }
 
 // read candidate c of the view; returns its (src, dst, time)
-template <int K>
-__device__ __forceinline__ void read_cand(const GraphDev& G, const LevelPlan& P,
+template <typename TT, int K>
+__device__ __forceinline__ void read_cand(const GraphDevT<TT>& G, const LevelPlan& P,
                                           const int32_t (&phi)[K], int64_t c, int32_t& s,
                                           int32_t& d, int64_t& tc) {
     if (P.view == kPair) {
@@ -186,7 +190,8 @@ __device__ __forceinline__ void read_cand(const GraphDev& G, const LevelPlan& P,
 }
 
 // the first edge at position e of the order the query enumerates first edges in
-__device__ __forceinline__ void first_edge(const GraphDev& G, int order, int64_t e, int32_t& s,
+template <typename TT>
+__device__ __forceinline__ void first_edge(const GraphDevT<TT>& G, int order, int64_t e, int32_t& s,
                                            int32_t& d, int64_t& t) {
     if (order == kOrdOut) {
         s = __ldg(G.out_src + e); d = __ldg(G.out_nbr + e); t = __ldg(G.out_t + e);
@@ -212,8 +217,8 @@ __device__ __forceinline__ bool check_bind(const LevelPlan& P, int32_t (&phi)[K]
 // exact count of the last motif edge's candidates in (tprev, thi] when one
 // endpoint is new: the range length minus the entries whose new endpoint is
 // already bound (those are exactly the pair segments to bound nodes)
-template <int K>
-__device__ __forceinline__ int64_t last_count_subtract(const GraphDev& G, const LevelPlan& P,
+template <typename TT, int K>
+__device__ __forceinline__ int64_t last_count_subtract(const GraphDevT<TT>& G, const LevelPlan& P,
                                                        const int32_t (&phi)[K], int64_t len,
                                                        int64_t tprev, int64_t thi) {
     int64_t excl = 0;
@@ -357,6 +362,22 @@ __device__ __forceinline__ int64_t warp_incl_scan64(int64_t v) {
     return v;
 }
 
+// Query plans staged in shared memory when the batch is small enough (every
+// item reads its plan; the block copies them once).
+constexpr int kSmemPlans = 64;
+
+__device__ __forceinline__ const QPlan* stage_plans(const QPlan* gplans, int nq, unsigned char* smem) {
+    if (nq > kSmemPlans) return gplans;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(gplans);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(smem);
+    int words = nq * (int)(sizeof(QPlan) / 8);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return reinterpret_cast<const QPlan*>(smem);
+}
+
+size_t plan_smem_bytes(int nq) { return nq <= kSmemPlans ? sizeof(QPlan) * (size_t)nq : 0; }
+
 // ----------------------------------------------------------------- kernels
 __global__ void k_wtab(uint64_t* __restrict__ tab, int64_t delta, int64_t cd) {
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d <= delta;
@@ -379,7 +400,8 @@ __global__ void k_wtab(uint64_t* __restrict__ tab, int64_t delta, int64_t cd) {
     }
 }
 
-__global__ void k_windows(GraphDev G, const QPlan* __restrict__ plans, int nq, WinDev W, int64_t NW) {
+template <typename TT>
+__global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int nq, WinDev W, int64_t NW) {
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < NW;
          w += (int64_t)gridDim.x * blockDim.x) {
         int lo_q = 0, hi_q = nq;
@@ -419,10 +441,13 @@ __global__ void k_windows(GraphDev G, const QPlan* __restrict__ plans, int nq, W
 }
 
 // one warp-uniform grid-stride loop over first edges f
-__global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict__ fwin,
+template <typename TT>
+__global__ void __launch_bounds__(256) k_level2(MatchArgs<TT> A, int32_t* __restrict__ fwin,
                                                 int64_t* __restrict__ len2, int64_t* __restrict__ lo2,
                                                 int64_t* __restrict__ hs_a, int64_t* __restrict__ hs_hi) {
-    const GraphDev& G = A.G;
+    const GraphDevT<TT>& G = A.G;
+    extern __shared__ __align__(16) unsigned char smem_plans[];
+    const QPlan* PL = stage_plans(A.plans, A.nq, smem_plans);
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -434,14 +459,28 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict
         int64_t f = base + lane;
         bool valid = f < F;
         int64_t wi = -1;
-        if (valid) {
+        // window of the warp's first edge by one binary search; lanes past its end search on
+        int64_t w0 = 0;
+        if (lane == 0) {
             int64_t lo = 0, hi = A.NW;
-            // last window whose fbase <= f
             while (hi - lo > 1) {
                 int64_t mid = (lo + hi) >> 1;
-                if (__ldg(A.W.fbase + mid) <= f) lo = mid; else hi = mid;
+                if (__ldg(A.W.fbase + mid) <= base) lo = mid; else hi = mid;
             }
-            wi = lo;
+            w0 = lo;
+        }
+        w0 = __shfl_sync(kFull, w0, 0);
+        if (valid) {
+            if (f < __ldg(A.W.fbase + w0) + __ldg(A.W.nfirst + w0)) {
+                wi = w0;
+            } else {
+                int64_t lo = w0, hi = A.NW;   // last window whose fbase <= f
+                while (hi - lo > 1) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (__ldg(A.W.fbase + mid) <= f) lo = mid; else hi = mid;
+                }
+                wi = lo;
+            }
         }
         // flush when any lane changes window
         if (__any_sync(kFull, valid && acc.win != wi)) {
@@ -449,7 +488,7 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict
             if (valid) acc.win = wi;
         }
         if (!valid) continue;
-        const QPlan& Q = A.plans[A.W.q[wi]];
+        const QPlan& Q = PL[A.W.q[wi]];
         int64_t e1 = A.W.lo[wi] + (f - A.W.fbase[wi]);
         int32_t s1, d1;
         int64_t t1;
@@ -481,7 +520,7 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict
                     const LevelPlan L = Q.lv[2];
                     bool x_src = L.su == 2;
                     int32_t bn = x_src ? phi_get(phi, L.sv) : phi_get(phi, L.su);
-                    const int64_t* ta = x_src ? G.in_t : G.out_t;
+                    const TT* ta = x_src ? G.in_t : G.out_t;
                     const int64_t* off = x_src ? G.in_off : G.out_off;
                     int64_t a = __ldg(off + bn), b = __ldg(off + bn + 1);
                     int64_t rlo = upper_bound_i64(ta, a, b, t1);
@@ -530,16 +569,16 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs A, int32_t* __restrict
 // Warp-cooperative expansion of motif edge D (0-based) for the 32 partial
 // instances held by the lanes (valid ones have edges 0..D-1 matched).
 // (ha, hh): the closing pair range when the query fixed it at the first edge.
-template <int D, int LMAX, int KMAX>
-__device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
+template <typename TT, int D, int LMAX, int KMAX>
+__device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, bool valid, int32_t q, int64_t win,
                        int32_t (&phi)[KMAX], int64_t t1, int64_t tprev, int64_t thi, int64_t ha,
                        int64_t hh, Acc& acc) {
-    const GraphDev& G = A.G;
+    const GraphDevT<TT>& G = A.G;
     int lane = threadIdx.x & 31;
     int64_t lo = 0, len = 0;
     int dir = 0;   // 1: this lane's candidates are the last edge's (two-sided closing)
     if (valid) {
-        const QPlan& Q = A.plans[q];
+        const QPlan& Q = PL[q];
         const LevelPlan P = Q.lv[D];
         if (D == Q.l - 1 && Q.hoist) {
             lo = upper_bound_i64(G.pair_t, ha, hh, tprev);
@@ -555,7 +594,7 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
                 int xl = P.bind_u ? P.su : P.sv;
                 bool x_src = L.su == xl;
                 int32_t bn = x_src ? phi_get(phi, L.sv) : phi_get(phi, L.su);
-                const int64_t* ta = x_src ? G.in_t : G.out_t;
+                const TT* ta = x_src ? G.in_t : G.out_t;
                 const int64_t* off = x_src ? G.in_off : G.out_off;
                 int64_t a = __ldg(off + bn), b = __ldg(off + bn + 1);
                 int64_t rlo = upper_bound_i64(ta, a, b, tprev);
@@ -616,7 +655,7 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
         bool ok = false, deeper = false;
         int64_t tc = 0;
         if (has) {
-            const QPlan& Q = A.plans[oq];
+            const QPlan& Q = PL[oq];
             const LevelPlan P = Q.lv[D];
             acc_switch(acc, ow, A.W.acc);
             if (odir) {
@@ -665,15 +704,17 @@ __device__ void expand(const MatchArgs& A, bool valid, int32_t q, int64_t win,
         }
         if constexpr (D + 1 < LMAX) {
             if (__any_sync(kFull, deeper))
-                expand<D + 1, LMAX, KMAX>(A, deeper, oq, ow, ophi, ot1, tc, othi, oha, ohh, acc);
+                expand<TT, D + 1, LMAX, KMAX>(A, PL, deeper, oq, ow, ophi, ot1, tc, othi, oha, ohh, acc);
         }
     }
 }
 
 // three-edge motifs fit in 64 registers: ask for four resident 256-thread blocks per SM
-template <int LMAX, int KMAX>
-__global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs A) {
-    const GraphDev& G = A.G;
+template <typename TT, int LMAX, int KMAX>
+__global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs<TT> A) {
+    const GraphDevT<TT>& G = A.G;
+    extern __shared__ __align__(16) unsigned char smem_plans[];
+    const QPlan* PL = stage_plans(A.plans, A.nq, smem_plans);
     int lane = threadIdx.x & 31;
     int64_t W2 = *A.d_W2;
     const int64_t F = A.d_F ? *A.d_F : A.F;
@@ -693,9 +734,23 @@ __global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs A)
         }
         fe = __shfl_sync(kFull, fb, 1);
         fb = __shfl_sync(kFull, fb, 0);
+        int64_t fcur = fb;   // first edge of the round's first item
         for (int64_t base = c0; base < c1; base += 32) {
             int64_t w = base + lane;
             bool valid = w < c1;
+            // first edges fcur .. fcur+31 in registers; each lane finds its item's
+            // first edge among them by a shuffle search (falls back past them)
+            int64_t ex = (fcur + lane <= fe) ? __ldg(A.excl + fcur + lane) : INT64_MAX;
+            int k = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                int64_t v = __shfl_sync(kFull, ex, k + step - 1);
+                if (v <= w) k += step;
+            }
+            int64_t last32 = __shfl_sync(kFull, ex, 31);
+            int64_t fw = fcur + k - 1;
+            if (valid && last32 <= w) fw = upper_bound_i64(A.excl, fcur + 31, fe + 1, w) - 1;
+            fcur = __shfl_sync(kFull, fw, 31);
             int32_t q = 0;
             int64_t win = -1, t1 = 0, thi = 0, tc = 0, ha = 0, hh = 0;
             int32_t phi[KMAX];
@@ -703,10 +758,10 @@ __global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs A)
             for (int i = 0; i < KMAX; i++) phi[i] = -1;
             bool deeper = false;
             if (valid) {
-                int64_t f = upper_bound_i64(A.excl, fb, fe + 1, w) - 1;
+                int64_t f = fw;
                 win = A.fwin[f];
                 q = A.W.q[win];
-                const QPlan& Q = A.plans[q];
+                const QPlan& Q = PL[q];
                 int64_t e1 = A.W.lo[win] + (f - A.W.fbase[win]);
                 first_edge(G, Q.order, e1, phi[0], phi[1], t1);
                 thi = min(t1 + Q.delta, A.W.tend[win]);
@@ -763,7 +818,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs A)
                 }
             }
             if (__any_sync(kFull, deeper))
-                expand<2, LMAX, KMAX>(A, deeper, q, win, phi, t1, tc, thi, ha, hh, acc);
+                expand<TT, 2, LMAX, KMAX>(A, PL, deeper, q, win, phi, t1, tc, thi, ha, hh, acc);
         }
         acc_flush_warp(acc, A.W.acc);
     }
@@ -871,8 +926,8 @@ __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __r
 }
 
 // ------------------------------------------------------- plain baseline K10
-template <int D, int LMAX>
-__device__ int64_t plain_dfs(const GraphDev& G, const QPlan& Q, int32_t (&phi)[TM_K_MAX],
+template <typename TT, int D, int LMAX>
+__device__ int64_t plain_dfs(const GraphDevT<TT>& G, const QPlan& Q, int32_t (&phi)[TM_K_MAX],
                              int64_t tprev, int64_t thi) {
     const LevelPlan P = Q.lv[D];
     int64_t lo, len;
@@ -890,13 +945,14 @@ __device__ int64_t plain_dfs(const GraphDev& G, const QPlan& Q, int32_t (&phi)[T
         if (D == Q.l - 1) {
             c += 1;
         } else if constexpr (D + 1 < LMAX) {
-            c += plain_dfs<D + 1, LMAX>(G, Q, nphi, tc, thi);
+            c += plain_dfs<TT, D + 1, LMAX>(G, Q, nphi, tc, thi);
         }
     }
     return c;
 }
 
-__global__ void k_plain(GraphDev G, const QPlan* __restrict__ plan, unsigned long long* out) {
+template <typename TT>
+__global__ void k_plain(GraphDevT<TT> G, const QPlan* __restrict__ plan, unsigned long long* out) {
     const QPlan& Q = *plan;
     unsigned long long c = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < G.m;
@@ -909,8 +965,8 @@ __global__ void k_plain(GraphDev G, const QPlan* __restrict__ plan, unsigned lon
         for (int i = 0; i < TM_K_MAX; i++) phi[i] = -1;
         phi[0] = s1;
         phi[1] = d1;
-        int64_t t1 = G.t[e];
-        c += (unsigned long long)plain_dfs<1, TM_L_MAX>(G, Q, phi, t1, t1 + Q.delta);
+        int64_t t1 = (int64_t)G.t[e];
+        c += (unsigned long long)plain_dfs<TT, 1, TM_L_MAX>(G, Q, phi, t1, t1 + Q.delta);
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
@@ -991,8 +1047,9 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
 
 }  // namespace
 
-int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
-              BatchOut* dbg) {
+template <typename TT>
+int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
+                BatchOut* dbg) {
     if (!g || (!qs && nq > 0) || (!res && nq > 0) || nq < 0) { set_error("NULL argument"); return TM_EINVAL; }
     if (nq == 0) return TM_OK;
     const Tuning tu = tuning();
@@ -1063,7 +1120,7 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
     };
     PhaseEvents pe(profiling());
     auto wall0 = std::chrono::steady_clock::now();
-    int ev_w0 = pe.mark(st), ev_w1 = -1, ev_l0 = -1, ev_l1 = -1, ev_m1 = -1, ev_f1 = -1;
+    int ev_w0 = pe.mark(st), ev_w1 = -1, ev_l0 = -1, ev_l1 = -1, ev_l2 = -1, ev_m1 = -1, ev_f1 = -1;
     int64_t hW2 = 0;
     fail(cudaMemcpyAsync(dplans, hp.data(), sizeof(QPlan) * (size_t)nq, cudaMemcpyHostToDevice, st), "plans");
     fail(cudaMemsetAsync(W.acc, 0, 8 * A_N * NWs, st), "acc");
@@ -1077,11 +1134,11 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
             fail(cudaGetLastError(), "k_wtab");
         }
     }
-    GraphDev G = g->dev;
+    GraphDevT<TT> G = typed<TT>(g->dev);
     int nsm = sm_count();
     if (rc == TM_OK && NW > 0) {
         unsigned gr = (unsigned)std::min<int64_t>((NW + 255) / 256, (int64_t)nsm * 16);
-        k_windows<<<gr, 256, 0, st>>>(G, dplans, nq, W, NW); count_launch();
+        k_windows<TT><<<gr, 256, 0, st>>>(G, dplans, nq, W, NW); count_launch();
         fail(cudaGetLastError(), "k_windows");
     }
     if (rc == TM_OK) rc = scan_exclusive_i64(W.nfirst, W.fbase, NW, dF, st);
@@ -1104,7 +1161,7 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
             int64_t* excl = (int64_t*)take2(8 * Fs);   // range lengths, then their exclusive scan in place
             int64_t* hs_a = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             int64_t* hs_hi = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
-            MatchArgs A;
+            MatchArgs<TT> A;
             A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = F; A.d_F = nullptr;
             A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
             A.d_W2 = dW2; A.counter = dctr;
@@ -1112,18 +1169,19 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
             int bt = tu.block_threads;
             int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
             ev_l0 = pe.mark(st);
-            k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
+            k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
             fail(cudaGetLastError(), "k_level2");
+            ev_l2 = pe.mark(st);
             if (rc == TM_OK) rc = scan_exclusive_i64(excl, excl, F, dW2, st);
             ev_l1 = pe.mark(st);
             if (rc == TM_OK) {
                 int bps = tu.blocks_per_sm;
                 A.chunk = tu.chunk_items;
                 unsigned gm = (unsigned)(nsm * bps);
-                if (lmax <= 3 && kmax <= 4) k_match<3, 4><<<gm, bt, 0, st>>>(A);
-                else if (lmax <= 4 && kmax <= 4) k_match<4, 4><<<gm, bt, 0, st>>>(A);
-                else if (lmax <= 4) k_match<4, TM_K_MAX><<<gm, bt, 0, st>>>(A);
-                else k_match<TM_L_MAX, TM_K_MAX><<<gm, bt, 0, st>>>(A);
+                if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 count_launch();
                 fail(cudaGetLastError(), "k_match");
                 ev_m1 = pe.mark(st);
@@ -1168,7 +1226,7 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
     fail(se, "batch sync");
     if (pe.on && rc == TM_OK) {
         double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
-        store_profile_batch(pe.ms(ev_w0, ev_w1), pe.ms(ev_l0, ev_l1), ev_l1 >= 0 ? pe.ms(ev_l1, ev_m1) : 0.0,
+        store_profile_batch(pe.ms(ev_w0, ev_w1), pe.ms(ev_l0, ev_l2), ev_l1 >= 0 ? pe.ms(ev_l1, ev_m1) : 0.0,
                             pe.ms(ev_m1 >= 0 && ev_l1 >= 0 ? ev_m1 : ev_f1, ev_f1), wall, hW2, F);
     }
     if (fb) cudaFreeAsync(fb, st);
@@ -1209,7 +1267,14 @@ int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cud
     return first_err;
 }
 
-int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* count) {
+int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
+              BatchOut* dbg) {
+    if (g && g->dev.tbytes == 4) return run_batch_t<int32_t>(g, qs, nq, res, st, dbg);
+    return run_batch_t<int64_t>(g, qs, nq, res, st, dbg);
+}
+
+template <typename TT>
+int count_plain_t(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* count) {
     if (!g || !m || !count) { set_error("NULL argument"); return TM_EINVAL; }
     if (delta < 0 || delta >= ((int64_t)1 << 61)) { set_error("delta outside [0, 2^61)"); return TM_EINVAL; }
     tm_query q;
@@ -1230,7 +1295,7 @@ int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* co
     if (e == cudaSuccess && g->m > 0) {
         int nsm = sm_count();
         unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, (int64_t)nsm * 8));
-        k_plain<<<gr, 256, 0, st>>>(g->dev, (const QPlan*)sb, dc); count_launch();
+        k_plain<TT><<<gr, 256, 0, st>>>(typed<TT>(g->dev), (const QPlan*)sb, dc); count_launch();
         e = cudaGetLastError();
     }
     unsigned long long hc = 0;
@@ -1245,6 +1310,11 @@ int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* co
         *count = (int64_t)hc;
     }
     return rc;
+}
+
+int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* count) {
+    if (g && g->dev.tbytes == 4) return count_plain_t<int32_t>(g, m, delta, count);
+    return count_plain_t<int64_t>(g, m, delta, count);
 }
 
 }  // namespace tmo
@@ -1304,8 +1374,9 @@ int na_scratch(unsigned char** out) {
     return TM_OK;
 }
 
-int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cudaStream_t st,
-                        int64_t* count) {
+template <typename TT>
+int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, cudaStream_t st,
+                          int64_t* count) {
     if (!g || !m || !count) return TM_EINVAL;
     if (delta < 0 || delta >= ((int64_t)1 << 61)) return TM_EINVAL;
     if (g->m > kNaMaxEdges) return TM_EINVAL;
@@ -1354,8 +1425,8 @@ int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cud
     if (e == cudaSuccess) e = cudaMemsetAsync(W.acc, 0, 8 * A_N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dctr, 0, 8, st);
     if (e != cudaSuccess) return na_status(e);
-    GraphDev G = g->dev;
-    k_windows<<<1, 32, 0, st>>>(G, dplan, 1, W, 1); count_launch();
+    GraphDevT<TT> G = typed<TT>(g->dev);
+    k_windows<TT><<<1, 32, 0, st>>>(G, dplan, 1, W, 1); count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_status(e);
     rc = scan_exclusive_i64_ws(W.nfirst, W.fbase, 1, dF, ws, kNaWsElems, st);
@@ -1363,7 +1434,7 @@ int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cud
     int64_t F = g->m;   // one window holding every edge
     if (F > 0) {
         const Tuning tu = tuning();
-        MatchArgs A;
+        MatchArgs<TT> A;
         A.G = G; A.plans = dplan; A.nq = 1; A.W = W; A.NW = 1; A.F = F; A.d_F = nullptr;
         A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
         A.hs_a = nullptr; A.hs_hi = nullptr;
@@ -1371,17 +1442,17 @@ int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cud
         A.chunk = tu.chunk_items;
         int nsm = sm_count();
         int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
-        k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, len2, lo2, nullptr, nullptr);
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, len2, lo2, nullptr, nullptr);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
         rc = scan_exclusive_i64_ws(len2, excl, F, dW2, ws, kNaWsElems, st);
         if (rc != TM_OK) return rc;
         unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
-        if (P.l <= 3 && P.k <= 4) k_match<3, 4><<<gm, tu.block_threads, 0, st>>>(A);
-        else if (P.l <= 4 && P.k <= 4) k_match<4, 4><<<gm, tu.block_threads, 0, st>>>(A);
-        else if (P.l <= 4) k_match<4, TM_K_MAX><<<gm, tu.block_threads, 0, st>>>(A);
-        else k_match<TM_L_MAX, TM_K_MAX><<<gm, tu.block_threads, 0, st>>>(A);
+        if (P.l <= 3 && P.k <= 4) k_match<TT, 3, 4><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
+        else if (P.l <= 4 && P.k <= 4) k_match<TT, 4, 4><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
+        else if (P.l <= 4) k_match<TT, 4, TM_K_MAX><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
+        else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
@@ -1395,6 +1466,12 @@ int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cud
     if (hres.status != TM_OK) return hres.status;
     *count = hres.count;
     return TM_OK;
+}
+
+int count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, cudaStream_t st,
+                        int64_t* count) {
+    if (g && g->dev.tbytes == 4) return count_exact_noalloc_t<int32_t>(g, m, delta, st, count);
+    return count_exact_noalloc_t<int64_t>(g, m, delta, st, count);
 }
 
 }  // namespace
@@ -1440,7 +1517,8 @@ void batch_release(tm_batch* b) {
     delete b;
 }
 
-int batch_create(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out) {
+template <typename TT>
+int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out) {
     if (!out) { set_error("out is NULL"); return TM_EINVAL; }
     *out = nullptr;
     if (!g || !qs || nq <= 0) { set_error("bad argument"); return TM_EINVAL; }
@@ -1543,7 +1621,7 @@ int batch_create(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out) 
     // captured sequence
     const Tuning tu = tuning();
     int nsm = sm_count();
-    GraphDev G = g->dev;
+    GraphDevT<TT> G = typed<TT>(g->dev);
     tm_profile pr0;
     tm_profile_last(&pr0);
     fail(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -1551,28 +1629,28 @@ int batch_create(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out) 
     fail(cudaMemsetAsync(dctr, 0, 8, st), "counter");
     if (rc == TM_OK && NW > 0) {
         unsigned gr = (unsigned)std::min<int64_t>((NW + 255) / 256, (int64_t)nsm * 16);
-        k_windows<<<gr, 256, 0, st>>>(G, dplans, nq, W, NW); count_launch();
+        k_windows<TT><<<gr, 256, 0, st>>>(G, dplans, nq, W, NW); count_launch();
         fail(cudaGetLastError(), "k_windows");
     }
     if (rc == TM_OK) rc = scan_exclusive_i64_ws(W.nfirst, W.fbase, NW, dF, wsp1, ws1, st);
     if (rc == TM_OK && Fmax > 0) {
-        MatchArgs A;
+        MatchArgs<TT> A;
         A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = Fmax; A.d_F = dF;
         A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
         A.d_W2 = dW2; A.counter = dctr;
         A.enum_threshold = tu.enum_threshold;
         A.chunk = tu.chunk_items;
         int64_t gl2 = std::min<int64_t>((Fmax + 255) / 256, (int64_t)nsm * 8);
-        k_level2<<<(unsigned)std::max<int64_t>(gl2, 1), 256, 0, st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
         fail(cudaGetLastError(), "k_level2");
         if (rc == TM_OK) rc = scan_exclusive_i64_dn(excl, excl, Fmax, dF, dW2, wsp2, ws2, st);
         if (rc == TM_OK) {
             unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
             int bt = tu.block_threads;
-            if (lmax <= 3 && kmax <= 4) k_match<3, 4><<<gm, bt, 0, st>>>(A);
-            else if (lmax <= 4 && kmax <= 4) k_match<4, 4><<<gm, bt, 0, st>>>(A);
-            else if (lmax <= 4) k_match<4, TM_K_MAX><<<gm, bt, 0, st>>>(A);
-            else k_match<TM_L_MAX, TM_K_MAX><<<gm, bt, 0, st>>>(A);
+            if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+            else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+            else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+            else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             count_launch();
             fail(cudaGetLastError(), "k_match");
         }
@@ -1598,6 +1676,11 @@ int batch_create(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out) 
     }
     *out = b;
     return TM_OK;
+}
+
+int batch_create(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out) {
+    if (g && g->dev.tbytes == 4) return batch_create_t<int32_t>(g, qs, nq, out);
+    return batch_create_t<int64_t>(g, qs, nq, out);
 }
 
 }  // namespace

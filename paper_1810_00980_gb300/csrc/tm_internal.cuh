@@ -34,28 +34,69 @@ int cuda_status(cudaError_t e, const char* what, const char* file, int line);
 // ----------------------------------------------------------------------------
 // device graph: edges sorted by time plus three time-sorted adjacency views
 // ----------------------------------------------------------------------------
+// Type-erased device graph: the time arrays hold int32 when every normalised
+// time fits (tbytes = 4), else int64 (tbytes = 8).
 struct GraphDev {
     int64_t m;
     int32_t n;
+    int32_t tbytes;         // 4 or 8: element size of t, out_t, in_t, pair_t
     int64_t P;              // distinct (src, dst) pairs
     const int32_t* src;     // [m]
     const int32_t* dst;     // [m]
-    const int64_t* t;       // [m] normalised, non-decreasing
+    const void* t;          // [m] normalised, non-decreasing
     const int64_t* out_off; // [n+1]
     const int32_t* out_nbr; // [m] destination
-    const int64_t* out_t;   // [m]
+    const void* out_t;      // [m]
     const int64_t* in_off;  // [n+1]
     const int32_t* in_nbr;  // [m] source
-    const int64_t* in_t;    // [m]
+    const void* in_t;       // [m]
     const int64_t* pk_off;  // [n+1] pair index range of each source
     const int32_t* pair_dst;// [P]
     const int64_t* pair_off;// [P+1]
-    const int64_t* pair_t;  // [m]
+    const void* pair_t;     // [m]
     const int32_t* out_src; // [m] source of each out-view entry (the sort key)
     const int32_t* in_dst;  // [m] destination of each in-view entry
     const unsigned long long* hslots;  // [2*(hmask+1)]: key, then (length << 32 | begin) of the pair's segment
     unsigned long long hmask;          // hash capacity - 1 (power of two)
 };
+
+// The same graph with its time arrays typed (TT = int32_t or int64_t).
+template <typename TT>
+struct GraphDevT {
+    int64_t m;
+    int32_t n;
+    int64_t P;
+    const int32_t* src;
+    const int32_t* dst;
+    const TT* t;
+    const int64_t* out_off;
+    const int32_t* out_nbr;
+    const TT* out_t;
+    const int64_t* in_off;
+    const int32_t* in_nbr;
+    const TT* in_t;
+    const int64_t* pk_off;
+    const int32_t* pair_dst;
+    const int64_t* pair_off;
+    const TT* pair_t;
+    const int32_t* out_src;
+    const int32_t* in_dst;
+    const unsigned long long* hslots;
+    unsigned long long hmask;
+};
+
+template <typename TT>
+inline GraphDevT<TT> typed(const GraphDev& g) {
+    GraphDevT<TT> r;
+    r.m = g.m; r.n = g.n; r.P = g.P;
+    r.src = g.src; r.dst = g.dst; r.t = (const TT*)g.t;
+    r.out_off = g.out_off; r.out_nbr = g.out_nbr; r.out_t = (const TT*)g.out_t;
+    r.in_off = g.in_off; r.in_nbr = g.in_nbr; r.in_t = (const TT*)g.in_t;
+    r.pk_off = g.pk_off; r.pair_dst = g.pair_dst; r.pair_off = g.pair_off; r.pair_t = (const TT*)g.pair_t;
+    r.out_src = g.out_src; r.in_dst = g.in_dst;
+    r.hslots = g.hslots; r.hmask = g.hmask;
+    return r;
+}
 
 constexpr unsigned long long kHashEmpty = ~0ull;
 
@@ -207,21 +248,23 @@ struct PhaseEvents {
 // ----------------------------------------------------------------------------
 // device helpers
 // ----------------------------------------------------------------------------
-// first index p in [lo, hi) with a[p] > v (a sorted non-decreasingly)
-__device__ __forceinline__ int64_t upper_bound_i64(const int64_t* __restrict__ a, int64_t lo,
-                                                   int64_t hi, int64_t v) {
+// first index p in [lo, hi) with a[p] > v (a sorted non-decreasingly; any integer element type)
+template <typename T>
+__device__ __forceinline__ int64_t upper_bound_i64(const T* __restrict__ a, int64_t lo, int64_t hi,
+                                                   int64_t v) {
     while (lo < hi) {
         int64_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(a + mid) <= v) lo = mid + 1; else hi = mid;
+        if ((int64_t)__ldg(a + mid) <= v) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 // first index p in [lo, hi) with a[p] >= v
-__device__ __forceinline__ int64_t lower_bound_i64(const int64_t* __restrict__ a, int64_t lo,
-                                                   int64_t hi, int64_t v) {
+template <typename T>
+__device__ __forceinline__ int64_t lower_bound_i64(const T* __restrict__ a, int64_t lo, int64_t hi,
+                                                   int64_t v) {
     while (lo < hi) {
         int64_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(a + mid) < v) lo = mid + 1; else hi = mid;
+        if ((int64_t)__ldg(a + mid) < v) lo = mid + 1; else hi = mid;
     }
     return lo;
 }

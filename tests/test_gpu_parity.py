@@ -353,3 +353,26 @@ def test_autotune_keeps_results(tm):
     assert tm.get_tuning() == best
     assert [r["count"] for r in tm.run_batch(g, qs)] == before
     tm.set_tuning(block_threads=256, blocks_per_sm=4, chunk_items=256, enum_threshold=48)
+
+
+def test_wide_time_span_uses_64_bit_times(tm, orc):
+    """Normalised spans >= 2^31 keep 64-bit time arrays; shorter spans use 32-bit
+    ones.  Both give the oracle's counts and estimates."""
+    rng = np.random.default_rng(31)
+    for span, burst, est in (((1 << 40), (1 << 34), ((1 << 20), 3, 0.01)),
+                             ((1 << 30), (1 << 20), ((1 << 18), 3, 0.5))):
+        n, m = 50, 6000
+        src = rng.integers(0, n, m)
+        dst = (src + 1 + rng.integers(0, n - 1, m)) % n
+        base = rng.integers(0, span, m // 20)
+        t = np.sort((np.repeat(base, 20) + rng.integers(0, burst, m)) % span).astype(np.int64)
+        src, dst = src.astype(np.int32), dst.astype(np.int32)
+        g = _graph(tm, src, dst, t)
+        delta = burst // 4
+        for name in ("cycle3", "outstar3", "pingpong", "cycle4"):
+            ms, md = synth.MOTIFS[name]
+            mo = tm.Motif(ms, md)
+            assert tm.count_exact(g, mo, delta) == orc.count_exact(src, dst, t, ms, md, delta)
+            d2, c2, p2 = est
+            z = tm.estimate(g, mo, d2, c2, p2, 17)
+            assert _close(z, orc.estimate(src, dst, t, ms, md, d2, c2, p2, 17))
