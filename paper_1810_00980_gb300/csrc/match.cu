@@ -37,13 +37,16 @@ namespace {
 
 constexpr int64_t kInf = INT64_MAX;
 constexpr int64_t kWtabMax = (int64_t)1 << 22;   // largest delta+1 given a weight table
+constexpr double kFullScanP = 0.25;              // keep rate from which windows enumerate by node
 
 // per-window accumulator fields
 enum { A_COUNT = 0, A_WLO, A_WHI, A_FIRST, A_CAND, A_LAST, A_INST, A_N };
 
 struct WinDev {
-    int64_t* lo;      // T_j = edges [lo, hi)
+    int64_t* lo;      // first edges of the window: positions [lo, hi) of the query's order
     int64_t* hi;
+    int64_t* tlo;     // T_j = edges [tlo, thi) of the time-sorted list
+    int64_t* thi;
     int64_t* tend;    // last admissible time (window end), kInf for exact
     int64_t* start;   // a_j
     int64_t* j;       // window index (1-based; 0 for exact)
@@ -416,6 +419,8 @@ __global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int 
         double qj;
         if (Q.mode == TM_MODE_EXACT) {
             k = 0; j = 0; start = 0; lo = 0; hi = G.m; tend = kInf; kept = 1; qj = 1.0;
+            W.tlo[w] = 0;
+            W.thi[w] = G.m;
         } else {
             k = (int32_t)(r / Q.J);
             j = r % Q.J + 1;
@@ -425,6 +430,16 @@ __global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int 
             tend = start + Q.cd - 1;
             lo = lower_bound_i64(G.t, 0, G.m, start);
             hi = upper_bound_i64(G.t, lo, G.m, tend);
+            W.tlo[w] = lo;
+            W.thi[w] = hi;
+            if (Q.full) {
+                // this window's node-grouped positions, partitioned per shift into perm
+                const int64_t* off = Q.woff + (int64_t)k * (Q.J + 1);
+                int64_t base = (int64_t)k * G.m;
+                int64_t a = off[j - 1], b = off[j];
+                lo = base + a;
+                hi = base + b;
+            }
             if (Q.q_mode == TM_Q_EDGES) {
                 qj = G.m > 0 ? Q.p * (double)(hi - lo) / (double)G.m : 0.0;
                 if (qj > 1.0) qj = 1.0;
@@ -440,9 +455,29 @@ __global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int 
     }
 }
 
+// window index (0-based) of every position of a node-grouped view for shift s
+template <typename TT>
+__global__ void k_winkey(const TT* __restrict__ tv, int64_t m, int64_t s, int64_t cd,
+                         uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        key[i] = (uint32_t)(((int64_t)tv[i] - s) / cd);
+        val[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_woff(const uint32_t* __restrict__ keys, int64_t m, int64_t nkeys, int64_t* __restrict__ off) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t prev = i == 0 ? -1 : (int64_t)keys[i - 1];
+        int64_t cur = i == m ? nkeys : (int64_t)keys[i];
+        for (int64_t v = prev + 1; v <= cur; v++) off[v] = i;
+    }
+}
+
 // one warp-uniform grid-stride loop over first edges f
 template <typename TT>
-__global__ void __launch_bounds__(256) k_level2(MatchArgs<TT> A, int32_t* __restrict__ fwin,
+__global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __restrict__ fwin,
                                                 int64_t* __restrict__ len2, int64_t* __restrict__ lo2,
                                                 int64_t* __restrict__ hs_a, int64_t* __restrict__ hs_hi) {
     const GraphDevT<TT>& G = A.G;
@@ -490,6 +525,7 @@ __global__ void __launch_bounds__(256) k_level2(MatchArgs<TT> A, int32_t* __rest
         if (!valid) continue;
         const QPlan& Q = PL[A.W.q[wi]];
         int64_t e1 = A.W.lo[wi] + (f - A.W.fbase[wi]);
+        if (Q.full) e1 = __ldg(Q.perm + e1);
         int32_t s1, d1;
         int64_t t1;
         first_edge(G, Q.order, e1, s1, d1, t1);
@@ -763,6 +799,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs<TT
                 q = A.W.q[win];
                 const QPlan& Q = PL[q];
                 int64_t e1 = A.W.lo[win] + (f - A.W.fbase[win]);
+                if (Q.full) e1 = __ldg(Q.perm + e1);
                 first_edge(G, Q.order, e1, phi[0], phi[1], t1);
                 thi = min(t1 + Q.delta, A.W.tend[win]);
                 int64_t l2 = A.lo2[f];
@@ -1042,6 +1079,20 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
         P.p = q.p;
         P.seed = q.seed;
         P.q_mode = q.q_mode;
+        // most windows kept: enumerate each window's first edges grouped by node
+        // (positions of the node-grouped view partitioned by window) instead of in time order
+        if (q.q_mode == TM_Q_UNIFORM && q.p >= kFullScanP && m->l >= 2 && g->m > 0 &&
+            P.J < (int64_t)1 << 31) {
+            const LevelPlan& L1 = m->lv[1];
+            int ord = kOrdTime;
+            if (L1.view == kOut) ord = L1.su == 0 ? kOrdOut : kOrdIn;
+            else if (L1.view == kIn) ord = L1.sv == 1 ? kOrdIn : kOrdOut;
+            else if (L1.view == kPair) ord = L1.su == 0 ? kOrdOut : kOrdIn;
+            if (ord != kOrdTime) {
+                P.order = ord;
+                P.full = 1;
+            }
+        }
     }
 }
 
@@ -1058,8 +1109,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     int first_err = TM_OK;
     int64_t NW = 0;
     int lmax = 1, kmax = 2;
-    bool any_hoist = false;
-    size_t wtab_bytes = 0;
+    bool any_hoist = false, any_full = false;
+    size_t wtab_bytes = 0, full_bytes = 0;
     for (int i = 0; i < nq; i++) {
         std::string why;
         int s = validate_query(g, qs[i], why);
@@ -1080,11 +1131,18 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         any_hoist |= hp[(size_t)i].hoist != 0;
         if (hp[(size_t)i].mode == TM_MODE_ESTIMATE && hp[(size_t)i].delta + 1 <= kWtabMax)
             wtab_bytes += a256(16 * (size_t)(hp[(size_t)i].delta + 1));
+        if (hp[(size_t)i].full) {
+            any_full = true;
+            full_bytes += a256(4 * (size_t)hp[(size_t)i].b * (size_t)g->m) +
+                          a256(8 * (size_t)hp[(size_t)i].b * (size_t)(hp[(size_t)i].J + 1));
+        }
     }
     // ---- scratch layout
     size_t NWs = (size_t)std::max<int64_t>(NW, 1);
+    size_t Ms = (size_t)std::max<int64_t>(g->m, 1);
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
-                7 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256;
+                9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
+                full_bytes + (any_full ? 3 * a256(4 * Ms) : 0);
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
     char* p = sb;
@@ -1096,10 +1154,19 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         if (P.l > 0 && P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) {
             P.wtab = (const uint64_t*)take(16 * (size_t)(P.delta + 1));
         }
+        if (P.full) {
+            P.perm = (const int32_t*)take(4 * (size_t)P.b * (size_t)g->m);
+            P.woff = (const int64_t*)take(8 * (size_t)P.b * (size_t)(P.J + 1));
+        }
     }
+    uint32_t* pk_key = any_full ? (uint32_t*)take(4 * Ms) : nullptr;
+    uint32_t* pk_ktmp = any_full ? (uint32_t*)take(4 * Ms) : nullptr;
+    uint32_t* pk_vtmp = any_full ? (uint32_t*)take(4 * Ms) : nullptr;
     WinDev W;
     W.lo = (int64_t*)take(8 * NWs);
     W.hi = (int64_t*)take(8 * NWs);
+    W.tlo = (int64_t*)take(8 * NWs);
+    W.thi = (int64_t*)take(8 * NWs);
     W.tend = (int64_t*)take(8 * NWs);
     W.start = (int64_t*)take(8 * NWs);
     W.j = (int64_t*)take(8 * NWs);
@@ -1136,6 +1203,28 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     GraphDevT<TT> G = typed<TT>(g->dev);
     int nsm = sm_count();
+    // dense-sampling queries: per shift, node-grouped view positions stably partitioned by window
+    for (int i = 0; i < nq && rc == TM_OK; i++) {
+        const QPlan& P = hp[(size_t)i];
+        if (!P.full || g->m == 0) continue;
+        const TT* tv = P.order == kOrdOut ? G.out_t : G.in_t;
+        int bits = 0;
+        while (bits < 31 && ((int64_t)1 << bits) < P.J) bits++;
+        for (int k = 0; k < P.b && rc == TM_OK; k++) {
+            int64_t sft = -(int64_t)(draw(P.seed, (uint64_t)k, 0) % (uint64_t)P.cd);
+            uint32_t* vals = (uint32_t*)(P.perm + (size_t)k * (size_t)g->m);
+            unsigned gr = (unsigned)std::min<int64_t>((g->m + 255) / 256, (int64_t)nsm * 8);
+            k_winkey<TT><<<gr, 256, 0, st>>>(tv, g->m, sft, P.cd, pk_key, vals); count_launch();
+            fail(cudaGetLastError(), "k_winkey");
+            if (rc == TM_OK) rc = radix_sort_pairs(pk_key, vals, pk_ktmp, pk_vtmp, g->m, bits, st);
+            if (rc == TM_OK) {
+                k_woff<<<(unsigned)std::min<int64_t>((g->m + 256) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
+                    pk_key, g->m, P.J, (int64_t*)(P.woff + (size_t)k * (size_t)(P.J + 1)));
+                count_launch();
+                fail(cudaGetLastError(), "k_woff");
+            }
+        }
+    }
     if (rc == TM_OK && NW > 0) {
         unsigned gr = (unsigned)std::min<int64_t>((NW + 255) / 256, (int64_t)nsm * 16);
         k_windows<TT><<<gr, 256, 0, st>>>(G, dplans, nq, W, NW); count_launch();
@@ -1212,8 +1301,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         h_lo.resize(n); h_hi.resize(n); h_start.resize(n); h_j.resize(n);
         h_k.resize(n); h_kept.resize(n); h_qj.resize(n); h_acc.resize(n * A_N);
         if (n) {
-            fail(cudaMemcpyAsync(h_lo.data(), W.lo + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
-            fail(cudaMemcpyAsync(h_hi.data(), W.hi + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_lo.data(), W.tlo + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
+            fail(cudaMemcpyAsync(h_hi.data(), W.thi + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
             fail(cudaMemcpyAsync(h_start.data(), W.start + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
             fail(cudaMemcpyAsync(h_j.data(), W.j + dq_base, 8 * n, cudaMemcpyDeviceToHost, st), "dbg");
             fail(cudaMemcpyAsync(h_k.data(), W.k + dq_base, 4 * n, cudaMemcpyDeviceToHost, st), "dbg");
@@ -1335,7 +1424,7 @@ namespace {
 constexpr size_t na_a256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int64_t kNaMaxEdges = TM_NOALLOC_MAX_EDGES;
 constexpr int64_t kNaWsElems = 2 * ((kNaMaxEdges + 2047) / 2048);
-constexpr size_t kNaWinBytes = 12 * 256 + na_a256(8 * tmo::A_N);
+constexpr size_t kNaWinBytes = 13 * 256 + na_a256(8 * tmo::A_N);
 constexpr size_t kNaBytes = na_a256(sizeof(tmo::QPlan)) + na_a256(sizeof(tm_result)) + kNaWinBytes +
                             3 * 256 + na_a256(4 * kNaMaxEdges) + 3 * na_a256(8 * kNaMaxEdges) +
                             na_a256(8 * kNaWsElems);
@@ -1390,6 +1479,8 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
     WinDev W;
     W.lo = (int64_t*)take(8);
     W.hi = (int64_t*)take(8);
+    W.tlo = (int64_t*)take(8);
+    W.thi = (int64_t*)take(8);
     W.tend = (int64_t*)take(8);
     W.start = (int64_t*)take(8);
     W.j = (int64_t*)take(8);
@@ -1399,7 +1490,6 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
     W.k = (int32_t*)take(4);
     W.kept = (int32_t*)take(4);
     W.qj = (double*)take(8);
-    take(8);  // keeps the window block at its documented size
     W.acc = (unsigned long long*)take(8 * A_N);
     int64_t* dF = (int64_t*)take(8);
     int64_t* dW2 = (int64_t*)take(8);
@@ -1544,6 +1634,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
             continue;
         }
         fill_plan(P, qs[i], g);
+        P.full = 0;
+        if (P.mode == TM_MODE_ESTIMATE) P.order = kOrdTime;
         P.win_base = NW;
         NW += P.mode == TM_MODE_EXACT ? 1 : P.J * P.b;
         Fmax += P.mode == TM_MODE_EXACT ? g->m : (int64_t)P.b * g->m;
@@ -1556,7 +1648,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     int64_t ws1 = 2 * ((NW + 2047) / 2048) + 2;
     int64_t ws2 = scan_dn_ws_elems(Fmax) + 2;
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
-                7 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
+                9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2);
     cudaError_t e = cudaMalloc(&b->scratch, sz);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_res, sizeof(tm_result) * (size_t)nq);
@@ -1578,6 +1670,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     WinDev W;
     W.lo = (int64_t*)take(8 * NWs);
     W.hi = (int64_t*)take(8 * NWs);
+    W.tlo = (int64_t*)take(8 * NWs);
+    W.thi = (int64_t*)take(8 * NWs);
     W.tend = (int64_t*)take(8 * NWs);
     W.start = (int64_t*)take(8 * NWs);
     W.j = (int64_t*)take(8 * NWs);

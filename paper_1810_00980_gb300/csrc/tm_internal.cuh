@@ -157,7 +157,9 @@ struct QPlan {
                          //    joins x to a first-edge node: instances can be closed from
                          //    either the second or the last edge's candidates
     int32_t rev2;        // 1: four or more edges, and the same holds for the last two
-    int32_t pad1;
+    int32_t full;        // 1: windows enumerate node-grouped positions through perm
+    const int32_t* perm; // [b*m] per shift: view positions stably partitioned by window
+    const int64_t* woff; // [b*(J+1)] per shift: start of each window's positions in perm
     int64_t delta;
     int64_t cd;          // c * delta (estimate), 0 for exact
     int64_t J;           // windows per shift (estimate), 1 for exact
