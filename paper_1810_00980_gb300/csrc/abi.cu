@@ -241,7 +241,7 @@ int tm_set_tuning(const tm_tuning* in) {
 int tm_autotune(const tm_graph* g, const tm_query* queries, int32_t n_queries, tm_tuning* best) {
     if (!g || !queries || n_queries <= 0 || !best) { set_error("bad argument"); return TM_EINVAL; }
     const int bts[] = {128, 256};
-    const int bpss[] = {2, 4, 8};
+    const int bpss[] = {2, 4, 6, 8};
     const int chunks[] = {64, 256, 1024};
     const int thr[] = {32, 128};
     std::vector<tm_result> res((size_t)n_queries);

@@ -27,16 +27,18 @@ __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __res
                            const int64_t* __restrict__ t, int64_t m, int32_t n_nodes,
                            int32_t* __restrict__ flags) {
     int32_t mx = -1;
-    int bad_sort = 0, bad_id = 0;
+    int bad_sort = 0, bad_id = 0, loop = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t s = src[i], d = dst[i];
         if (s < 0 || d < 0 || (n_nodes >= 0 && (s >= n_nodes || d >= n_nodes))) bad_id = 1;
         mx = max(mx, max(s, d));
+        loop |= s == d;
         if (i > 0 && t[i] < t[i - 1]) bad_sort = 1;
     }
     if (__any_sync(kFull, bad_sort) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1);
     if (__any_sync(kFull, bad_id) && (threadIdx.x & 31) == 0) atomicOr(&flags[1], 1);
+    if (__any_sync(kFull, loop) && (threadIdx.x & 31) == 0) atomicOr(&flags[3], 1);
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(&flags[2], mx);
 }
@@ -184,6 +186,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     PhaseEvents pe(profiling());
     int ev0 = pe.mark(st);
     int64_t tmin = 0, tmax = 0;
+    int32_t loops = 0;
     int32_t n = n_nodes < 0 ? 0 : n_nodes;
     if (m > 0) {
         int32_t* flags = nullptr;
@@ -205,6 +208,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         tmax = tt[1] - tt[0];
         if (tt[1] < tt[0] || tmax >= ((int64_t)1 << 61)) { set_error("time span >= 2^61"); return TM_EINVAL; }
         if (n_nodes < 0) n = hf[2] + 1;
+        loops = hf[3];
     }
 
     // ---- one allocation for the resident graph
@@ -251,7 +255,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     int32_t* in_dst = (int32_t*)take(sz_i32m);
 
     GraphDev& G = g->dev;
-    G.m = m; G.n = n; G.tbytes = tb;
+    G.m = m; G.n = n; G.tbytes = tb; G.loops = loops;
     G.src = gs; G.dst = gd; G.t = gt;
     G.out_off = out_off; G.out_nbr = out_nbr; G.out_t = out_t;
     G.in_off = in_off; G.in_nbr = in_nbr; G.in_t = in_t;

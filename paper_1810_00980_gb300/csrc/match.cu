@@ -576,7 +576,16 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                         ha = upper_bound_i64(G.pair_t, a0, b0, t1);
                         hh = gallop_ub(G.pair_t, ha, b0, thi);
                     }
-                    if (hh == ha) len = 0;   // no closing edge in time: no instance starts here
+                    if (hh == ha) {
+                        len = 0;                 // no closing edge in time: no instance starts here
+                    } else if (Q.hrev && hh - ha < len) {
+                        // fewer closing edges than second-edge candidates: the closing
+                        // edges become the items; keep the second-edge range for counting
+                        int64_t end1 = lo + len;
+                        lo = -1 - lo;
+                        len = hh - ha;
+                        hh = end1;
+                    }
                 }
                 if (Q.l == 2 && Q.mode == TM_MODE_EXACT) {
                     if (P.view == kPair) {
@@ -745,9 +754,10 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
     }
 }
 
-// three-edge motifs fit in 64 registers: ask for four resident 256-thread blocks per SM
-template <typename TT, int LMAX, int KMAX>
-__global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs<TT> A) {
+// OCC: resident 256-thread blocks per SM the register allocation must allow
+// (three-edge motifs: 4 without spills, 6 with a few spilled registers)
+template <typename TT, int LMAX, int KMAX, int OCC = (LMAX <= 3 ? 4 : 1)>
+__global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
     const GraphDevT<TT>& G = A.G;
     extern __shared__ __align__(16) unsigned char smem_plans[];
     const QPlan* PL = stage_plans(A.plans, A.nq, smem_plans);
@@ -803,7 +813,36 @@ __global__ void __launch_bounds__(256, (LMAX <= 3 ? 4 : 1)) k_match(MatchArgs<TT
                 first_edge(G, Q.order, e1, phi[0], phi[1], t1);
                 thi = min(t1 + Q.delta, A.W.tend[win]);
                 int64_t l2 = A.lo2[f];
-                if (l2 < 0) {
+                if (l2 < 0 && Q.hoist) {
+                    // closing edge e3 of the first edge's pair: count the valid second
+                    // edges with time in (t1, t3)
+                    const LevelPlan L = Q.lv[2];
+                    const LevelPlan M1 = Q.lv[1];
+                    int64_t lo1 = -1 - l2, end1 = A.hs_hi[f], ha0 = A.hs_a[f];
+                    int64_t p3 = ha0 + (w - A.excl[f]);
+                    int64_t t3 = __ldg(G.pair_t + p3);
+                    acc_switch(acc, win, A.W.acc);
+                    acc.f[A_CAND] += 1;
+                    acc.f[A_LAST] += 1;
+                    const TT* t1v = M1.view == kPair ? G.pair_t : M1.view == kOut ? G.out_t : G.in_t;
+                    int64_t cnt = upper_bound_i64(t1v, lo1, end1, t3 - 1) - lo1;
+                    if (M1.view != kPair) {
+                        // second edges whose new node would be a first-edge node are invalid
+                        int32_t bn = M1.view == kOut ? phi_get(phi, M1.su) : phi_get(phi, M1.sv);
+                        int32_t hu = phi_get(phi, L.su), hv = phi_get(phi, L.sv);
+#pragma unroll
+                        for (int y = 0; y < 2; y++) {
+                            int32_t xs = M1.view == kOut ? bn : phi[y];
+                            int32_t xd = M1.view == kOut ? phi[y] : bn;
+                            if (xs == hu && xd == hv) cnt -= lower_bound_i64(G.pair_t, ha0, p3, t3) - ha0;
+                            else if (xs != xd || G.loops) cnt -= pair_count(G, xs, xd, t1, t3 - 1);
+                        }
+                    }
+                    if (cnt) {
+                        acc.f[A_COUNT] += cnt;
+                        if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                    }
+                } else if (l2 < 0) {
                     // closing-edge candidate e3 = (x, t3); count second edges in (t1, t3)
                     const LevelPlan L = Q.lv[2];
                     const LevelPlan M1 = Q.lv[1];
@@ -1047,6 +1086,12 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
         const LevelPlan& L = m->lv[m->l - 1];
         P.hoist = (L.view == kPair && L.su <= 1 && L.sv <= 1) ? 1 : 0;
     }
+    P.hrev = 0;
+    if (m->l == 3 && P.hoist) {
+        const LevelPlan& L1 = m->lv[1];
+        bool one_new = (L1.view == kOut || L1.view == kIn) && (L1.bind_u + L1.bind_v == 1);
+        P.hrev = (L1.view == kPair || one_new) ? 1 : 0;
+    }
     P.rev2 = 0;
     if (m->l >= 4) {
         const LevelPlan& LD = m->lv[m->l - 2];
@@ -1267,7 +1312,9 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 int bps = tu.blocks_per_sm;
                 A.chunk = tu.chunk_items;
                 unsigned gm = (unsigned)(nsm * bps);
-                if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
+                    k_match<TT, 3, 4, 6><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
@@ -1741,7 +1788,9 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         if (rc == TM_OK) {
             unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
             int bt = tu.block_threads;
-            if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+            if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
+                k_match<TT, 3, 4, 6><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+            else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);

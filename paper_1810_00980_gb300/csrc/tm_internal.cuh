@@ -58,6 +58,7 @@ struct GraphDev {
     const int32_t* in_dst;  // [m] destination of each in-view entry
     const unsigned long long* hslots;  // [2*(hmask+1)]: key, then (length << 32 | begin) of the pair's segment
     unsigned long long hmask;          // hash capacity - 1 (power of two)
+    int32_t loops;          // 1 if some edge has src == dst
 };
 
 // The same graph with its time arrays typed (TT = int32_t or int64_t).
@@ -83,6 +84,7 @@ struct GraphDevT {
     const int32_t* in_dst;
     const unsigned long long* hslots;
     unsigned long long hmask;
+    int32_t loops;
 };
 
 template <typename TT>
@@ -94,7 +96,7 @@ inline GraphDevT<TT> typed(const GraphDev& g) {
     r.in_off = g.in_off; r.in_nbr = g.in_nbr; r.in_t = (const TT*)g.in_t;
     r.pk_off = g.pk_off; r.pair_dst = g.pair_dst; r.pair_off = g.pair_off; r.pair_t = (const TT*)g.pair_t;
     r.out_src = g.out_src; r.in_dst = g.in_dst;
-    r.hslots = g.hslots; r.hmask = g.hmask;
+    r.hslots = g.hslots; r.hmask = g.hmask; r.loops = g.loops;
     return r;
 }
 
@@ -158,6 +160,10 @@ struct QPlan {
                          //    either the second or the last edge's candidates
     int32_t rev2;        // 1: four or more edges, and the same holds for the last two
     int32_t full;        // 1: windows enumerate node-grouped positions through perm
+    int32_t hrev;        // 1: three edges, closing pair fixed by the first edge, and the second
+                         //    edge either joins the first edge's nodes or adds one node: the
+                         //    closing pair's entries can be the items instead
+    int32_t pad2;
     const int32_t* perm; // [b*m] per shift: view positions stably partitioned by window
     const int64_t* woff; // [b*(J+1)] per shift: start of each window's positions in perm
     int64_t delta;

@@ -30,6 +30,8 @@ MOTIFS = [
     ([0, 1, 0], [1, 2, 2]),          # a->b, b->c, a->c
     ([0, 0, 1], [1, 2, 2]),          # a->b, a->c, b->c
     ([2, 2, 2], [0, 1, 0]),
+    ([0, 2, 0], [1, 1, 1]),          # b->a, c->a, b->a: closing pair fixed, second edge into a
+    ([0, 0, 1], [1, 2, 0]),          # c->a, c->b, a->c: closing pair is the reverse pair
     ([0, 1, 0], [1, 0, 1]),
     ([0, 2, 1], [1, 3, 2]),
     ([0, 1, 2, 3], [1, 2, 3, 0]),
@@ -104,8 +106,8 @@ def test_exact_mid_graph_all_config_motifs(tm, orc):
     """A bursty power-law graph spanning many matcher chunks and ragged tails."""
     src, dst, t = synth.chung_lu_hawkes(3000, 300_000, 2.1, seed=21, horizon=6_000_000)
     g = _graph(tm, src, dst, t)
-    for name in ("cycle3", "outstar3", "pingpong", "cycle4"):
-        ms, md = synth.MOTIFS[name]
+    for name in ("cycle3", "outstar3", "pingpong", "cycle4", "instar3"):
+        ms, md = synth.MOTIFS[name] if name in synth.MOTIFS else ([0, 2, 0], [1, 1, 1])
         mo = tm.Motif(ms, md)
         for delta in (600, 3600, 86400):
             want = orc.count_exact(src, dst, t, ms, md, delta, threads=8)
