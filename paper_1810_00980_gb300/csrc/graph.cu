@@ -150,6 +150,14 @@ __global__ void k_pair_src(const uint32_t* __restrict__ perm, const int32_t* __r
         if (head[i]) pair_src[pid_excl[i]] = src[perm[i]];
 }
 
+// pair index of every pair-view position: heads up to and including it, minus one
+__global__ void k_pair_pid(const int64_t* __restrict__ head, const int64_t* __restrict__ pid_excl, int64_t m,
+                           int32_t* __restrict__ pair_pid) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        pair_pid[i] = (int32_t)(pid_excl[i] + head[i] - 1);
+}
+
 __global__ void k_pair_tail(int64_t* __restrict__ pair_off, const int64_t* __restrict__ P, int64_t m) {
     pair_off[*P] = m;
 }
@@ -221,7 +229,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
                  + sz_off + sz_i32m + sz_tm     // out view
                  + sz_off + sz_i32m + sz_tm     // in view
                  + sz_off + sz_i32m + align256(8 * (M + 1)) + sz_tm   // pair view (P <= m)
-                 + 2 * sz_i32m;                                          // view keys
+                 + 3 * sz_i32m;                                          // view keys, pair index
     tm_graph* g = new (std::nothrow) tm_graph();
     if (!g) { set_error("host allocation failed"); return TM_ENOMEM; }
     g->device = dev;
@@ -253,6 +261,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     void* pair_t = take(sz_tm);
     int32_t* out_src = (int32_t*)take(sz_i32m);
     int32_t* in_dst = (int32_t*)take(sz_i32m);
+    int32_t* pair_pid = (int32_t*)take(sz_i32m);
 
     GraphDev& G = g->dev;
     G.m = m; G.n = n; G.tbytes = tb; G.loops = loops;
@@ -260,7 +269,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     G.out_off = out_off; G.out_nbr = out_nbr; G.out_t = out_t;
     G.in_off = in_off; G.in_nbr = in_nbr; G.in_t = in_t;
     G.pk_off = pk_off; G.pair_dst = pair_dst; G.pair_off = pair_off; G.pair_t = pair_t;
-    G.out_src = out_src; G.in_dst = in_dst;
+    G.out_src = out_src; G.in_dst = in_dst; G.pair_pid = pair_pid;
     G.hslots = nullptr; G.hmask = 0;
     g->hash_block = nullptr;
 
@@ -355,6 +364,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         k_pair_tail<<<1, 1, 0, st>>>(pair_off, dP, m); count_launch();
         k_pk_off<<<grid_for((int64_t)n + 1), kThreads, 0, st>>>(out_off, head, pid, dP, m, n, pk_off); count_launch();
         k_pair_src<<<gr, kThreads, 0, st>>>(vb, gs, head, pid, m, (int32_t*)kt); count_launch();
+        k_pair_pid<<<gr, kThreads, 0, st>>>(head, pid, m, pair_pid); count_launch();
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
     }
     int64_t P = 0;

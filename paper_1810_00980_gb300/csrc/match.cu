@@ -38,6 +38,7 @@ namespace {
 constexpr int64_t kInf = INT64_MAX;
 constexpr int64_t kWtabMax = (int64_t)1 << 22;   // largest delta+1 given a weight table
 constexpr double kFullScanP = 0.25;              // keep rate from which windows enumerate by node
+constexpr int64_t kRevMinLen = 8;                // shortest second-edge range worth closing from the other side
 
 // per-window accumulator fields
 enum { A_COUNT = 0, A_WLO, A_WHI, A_FIRST, A_CAND, A_LAST, A_INST, A_N };
@@ -200,6 +201,9 @@ __device__ __forceinline__ void first_edge(const GraphDevT<TT>& G, int order, in
         s = __ldg(G.out_src + e); d = __ldg(G.out_nbr + e); t = __ldg(G.out_t + e);
     } else if (order == kOrdIn) {
         s = __ldg(G.in_nbr + e); d = __ldg(G.in_dst + e); t = __ldg(G.in_t + e);
+    } else if (order == kOrdPair) {
+        // the pair view is grouped by source at the same positions as the out view
+        s = __ldg(G.out_src + e); d = __ldg(G.pair_dst + __ldg(G.pair_pid + e)); t = __ldg(G.pair_t + e);
     } else {
         s = __ldg(G.src + e); d = __ldg(G.dst + e); t = __ldg(G.t + e);
     }
@@ -539,7 +543,17 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
             } else {
                 int32_t phi[2] = {s1, d1};
                 const LevelPlan P = Q.lv[1];
-                if (Q.order == kOrdOut && P.view == kOut && P.su == 0) {
+                bool have_h = false;
+                if (Q.hoist && Q.order == kOrdPair) {
+                    // the closing pair is the first edge's own pair: its entries after e1 up to thi
+                    int64_t pend = __ldg(G.pair_off + __ldg(G.pair_pid + e1) + 1);
+                    ha = gallop_ub(G.pair_t, e1 + 1, pend, t1);
+                    hh = thi > t1 ? gallop_ub(G.pair_t, ha, pend, thi) : ha;
+                    have_h = true;
+                }
+                if (have_h && hh == ha) {
+                    len = 0;   // no closing edge in time: nothing else to look up
+                } else if (Q.order == kOrdOut && P.view == kOut && P.su == 0) {
                     // e1 is entry e1 of out(s1): its candidates start right after it
                     int64_t b = __ldg(G.out_off + s1 + 1);
                     lo = gallop_ub(G.out_t, e1 + 1, b, t1);
@@ -551,8 +565,9 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                 } else {
                     level_range(G, P, phi, t1, thi, lo, len);
                 }
-                if (Q.rev && len > 0) {
-                    // candidates of the last edge given only its first-edge node
+                if (Q.rev && len > kRevMinLen) {
+                    // candidates of the last edge given only its first-edge node (worth a
+                    // search only when the second-edge range is long)
                     const LevelPlan L = Q.lv[2];
                     bool x_src = L.su == 2;
                     int32_t bn = x_src ? phi_get(phi, L.sv) : phi_get(phi, L.su);
@@ -572,7 +587,7 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                     // the closing pair is fixed by the first edge: find its range once
                     const LevelPlan L = Q.lv[Q.l - 1];
                     int64_t a0, b0;
-                    if (pair_segment(G, phi_get(phi, L.su), phi_get(phi, L.sv), a0, b0)) {
+                    if (!have_h && pair_segment(G, phi_get(phi, L.su), phi_get(phi, L.sv), a0, b0)) {
                         ha = upper_bound_i64(G.pair_t, a0, b0, t1);
                         hh = gallop_ub(G.pair_t, ha, b0, thi);
                     }
@@ -1108,6 +1123,9 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
         bool closes_x = L2.view == kPair && ((L2.su == 2 && L2.sv <= 1) || (L2.sv == 2 && L2.su <= 1));
         P.rev = (one_new && closes_x) ? 1 : 0;
     }
+    // when the closing edge repeats the first edge's pair, first edges go in pair order:
+    // the closing range then starts right after the first edge's own position
+    bool own_pair = P.hoist && m->lv[m->l - 1].su == 0 && m->lv[m->l - 1].sv == 1;
     if (q.mode == TM_MODE_EXACT) {
         P.b = 1; P.cd = 0; P.J = 1; P.p = 1.0; P.q_mode = TM_Q_UNIFORM;
         // exact queries take first edges grouped by the node their second edge hangs off
@@ -1116,6 +1134,7 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
             if (L1.view == kOut) P.order = L1.su == 0 ? kOrdOut : kOrdIn;
             else if (L1.view == kIn) P.order = L1.sv == 1 ? kOrdIn : kOrdOut;
             else if (L1.view == kPair) P.order = L1.su == 0 ? kOrdOut : kOrdIn;
+            if (own_pair) P.order = kOrdPair;
         }
     } else {
         P.b = q.b;
@@ -1133,6 +1152,7 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
             if (L1.view == kOut) ord = L1.su == 0 ? kOrdOut : kOrdIn;
             else if (L1.view == kIn) ord = L1.sv == 1 ? kOrdIn : kOrdOut;
             else if (L1.view == kPair) ord = L1.su == 0 ? kOrdOut : kOrdIn;
+            if (own_pair) ord = kOrdPair;
             if (ord != kOrdTime) {
                 P.order = ord;
                 P.full = 1;
@@ -1252,7 +1272,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     for (int i = 0; i < nq && rc == TM_OK; i++) {
         const QPlan& P = hp[(size_t)i];
         if (!P.full || g->m == 0) continue;
-        const TT* tv = P.order == kOrdOut ? G.out_t : G.in_t;
+        const TT* tv = P.order == kOrdOut ? G.out_t : P.order == kOrdIn ? G.in_t : G.pair_t;
         int bits = 0;
         while (bits < 31 && ((int64_t)1 << bits) < P.J) bits++;
         for (int k = 0; k < P.b && rc == TM_OK; k++) {

@@ -174,7 +174,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;                       // per lane
 constexpr int kSortTile = kSortThreads * kSortItems; // 4096
-constexpr int kMaxDigitBits = 8;
+constexpr int kMaxDigitBits = 10;
 
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int db,
                              int32_t* __restrict__ hist, int64_t ntiles) {

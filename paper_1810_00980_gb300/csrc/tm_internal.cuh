@@ -56,6 +56,7 @@ struct GraphDev {
     const void* pair_t;     // [m]
     const int32_t* out_src; // [m] source of each out-view entry (the sort key)
     const int32_t* in_dst;  // [m] destination of each in-view entry
+    const int32_t* pair_pid;// [m] pair index of each pair-view entry
     const unsigned long long* hslots;  // [2*(hmask+1)]: key, then (length << 32 | begin) of the pair's segment
     unsigned long long hmask;          // hash capacity - 1 (power of two)
     int32_t loops;          // 1 if some edge has src == dst
@@ -82,6 +83,7 @@ struct GraphDevT {
     const TT* pair_t;
     const int32_t* out_src;
     const int32_t* in_dst;
+    const int32_t* pair_pid;
     const unsigned long long* hslots;
     unsigned long long hmask;
     int32_t loops;
@@ -95,7 +97,7 @@ inline GraphDevT<TT> typed(const GraphDev& g) {
     r.out_off = g.out_off; r.out_nbr = g.out_nbr; r.out_t = (const TT*)g.out_t;
     r.in_off = g.in_off; r.in_nbr = g.in_nbr; r.in_t = (const TT*)g.in_t;
     r.pk_off = g.pk_off; r.pair_dst = g.pair_dst; r.pair_off = g.pair_off; r.pair_t = (const TT*)g.pair_t;
-    r.out_src = g.out_src; r.in_dst = g.in_dst;
+    r.out_src = g.out_src; r.in_dst = g.in_dst; r.pair_pid = g.pair_pid;
     r.hslots = g.hslots; r.hmask = g.hmask; r.loops = g.loops;
     return r;
 }
@@ -146,7 +148,7 @@ namespace tmo {
 
 // order in which a query enumerates first edges: by time (windows), or grouped
 // by source / destination (positions of the out / in view) for exact queries
-enum FirstOrder : int32_t { kOrdTime = 0, kOrdOut = 1, kOrdIn = 2 };
+enum FirstOrder : int32_t { kOrdTime = 0, kOrdOut = 1, kOrdIn = 2, kOrdPair = 3 };
 
 struct QPlan {
     int32_t l, k;
