@@ -258,6 +258,9 @@ typedef struct {
     int64_t launches;       /* kernel launches since load */
 } tm_profile;
 int tm_profile_enable(int32_t on);
+/* Return device memory that freed graphs and batch scratch left in the library's
+ * stream-ordered pool (kept mapped for reuse) to the device.  Synchronises the device. */
+int tm_release_cached_memory(void);
 int tm_profile_last(tm_profile* out);
 
 /* ---- serving -----------------------------------------------------------------

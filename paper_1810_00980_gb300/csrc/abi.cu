@@ -303,6 +303,8 @@ int tm_profile_enable(int32_t on) {
     return TM_OK;
 }
 
+int tm_release_cached_memory(void) { return pool_trim(); }
+
 int tm_profile_last(tm_profile* out) {
     if (!out) { set_error("NULL argument"); return TM_EINVAL; }
     std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -544,11 +544,22 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                 int32_t phi[2] = {s1, d1};
                 const LevelPlan P = Q.lv[1];
                 bool have_h = false;
-                if (Q.hoist && Q.order == kOrdPair) {
-                    // the closing pair is the first edge's own pair: its entries after e1 up to thi
-                    int64_t pend = __ldg(G.pair_off + __ldg(G.pair_pid + e1) + 1);
-                    ha = gallop_ub(G.pair_t, e1 + 1, pend, t1);
-                    hh = thi > t1 ? gallop_ub(G.pair_t, ha, pend, thi) : ha;
+                if (Q.hoist) {
+                    // the closing pair is fixed by the first edge: find its range first, so
+                    // first edges with no closing edge skip every other search
+                    if (Q.order == kOrdPair) {
+                        // the first edge's own pair: its entries after e1 up to thi
+                        int64_t pend = __ldg(G.pair_off + __ldg(G.pair_pid + e1) + 1);
+                        ha = gallop_ub(G.pair_t, e1 + 1, pend, t1);
+                        hh = thi > t1 ? gallop_ub(G.pair_t, ha, pend, thi) : ha;
+                    } else {
+                        const LevelPlan L = Q.lv[Q.l - 1];
+                        int64_t a0, b0;
+                        if (thi > t1 && pair_segment(G, phi_get(phi, L.su), phi_get(phi, L.sv), a0, b0)) {
+                            ha = upper_bound_i64(G.pair_t, a0, b0, t1);
+                            hh = gallop_ub(G.pair_t, ha, b0, thi);
+                        }
+                    }
                     have_h = true;
                 }
                 if (have_h && hh == ha) {
@@ -584,13 +595,6 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                     }
                 }
                 if (Q.hoist && len > 0) {
-                    // the closing pair is fixed by the first edge: find its range once
-                    const LevelPlan L = Q.lv[Q.l - 1];
-                    int64_t a0, b0;
-                    if (!have_h && pair_segment(G, phi_get(phi, L.su), phi_get(phi, L.sv), a0, b0)) {
-                        ha = upper_bound_i64(G.pair_t, a0, b0, t1);
-                        hh = gallop_ub(G.pair_t, ha, b0, thi);
-                    }
                     if (hh == ha) {
                         len = 0;                 // no closing edge in time: no instance starts here
                     } else if (Q.hrev && hh - ha < len) {
@@ -1145,8 +1149,10 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
         P.q_mode = q.q_mode;
         // most windows kept: enumerate each window's first edges grouped by node
         // (positions of the node-grouped view partitioned by window) instead of in time order
+        // (only for windows large enough to hold, on average, an edge per node: smaller
+        // windows gain no locality from it and would pay for the partition)
         if (q.q_mode == TM_Q_UNIFORM && q.p >= kFullScanP && m->l >= 2 && g->m > 0 &&
-            P.J < (int64_t)1 << 31) {
+            P.J < (int64_t)1 << 31 && g->m / P.J >= (int64_t)g->n) {
             const LevelPlan& L1 = m->lv[1];
             int ord = kOrdTime;
             if (L1.view == kOut) ord = L1.su == 0 ? kOrdOut : kOrdIn;

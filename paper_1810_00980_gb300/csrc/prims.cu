@@ -419,6 +419,16 @@ void pool_free(void* p, int dev) {
     else cudaFree(p);
 }
 
+int pool_trim() {
+    int dev = 0;
+    TM_CUDA(cudaGetDevice(&dev));
+    TM_CUDA(cudaDeviceSynchronize());
+    cudaMemPool_t pool;
+    TM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    TM_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return TM_OK;
+}
+
 int sm_count() {
     static int n = 0;
     if (n == 0) {

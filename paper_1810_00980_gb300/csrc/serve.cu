@@ -4,6 +4,7 @@
 // run it on their own stream with run_batch, and publish the results.  While
 // one batch is on the GPU the other schedulers admit newly arrived queries,
 // so batches overlap on the device (continuous batching).
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -25,8 +26,26 @@ struct Ticket {
     int state = kQueued;
     int status = TM_PENDING;
     int64_t footprint = 0;
+    uint64_t cls = 0;     // query class (graph, motif, delta, mode, c, p, b, q rule)
+    double pred = 0.0;    // predicted work (first edges + candidates read)
     tm_result r{};
 };
+
+uint64_t class_key(int32_t gid, const tm_query& q) {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+    auto mixin = [&](uint64_t v) { h = tmo::sm64_mix(h ^ (v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2))); };
+    mixin((uint64_t)gid);
+    mixin((uint64_t)(uintptr_t)q.motif);
+    mixin((uint64_t)q.delta);
+    mixin((uint64_t)q.mode);
+    if (q.mode == TM_MODE_ESTIMATE) {
+        mixin((uint64_t)q.c);
+        mixin((uint64_t)(int64_t)(q.p * 1e6));
+        mixin((uint64_t)q.b);
+        mixin((uint64_t)q.q_mode);
+    }
+    return h;
+}
 
 }  // namespace
 
@@ -43,9 +62,12 @@ struct tm_server {
     int64_t in_use = 0;
     bool stopping = false;
     uint64_t next_id = 1;
+    std::unordered_map<uint64_t, double> work_ema;   // learned work per query class
 };
 
 namespace {
+
+constexpr double kWorkFloor = 2e8;   // predicted work always admitted into one batch
 
 // Upper estimate of the scratch a query needs inside run_batch.
 int64_t footprint(const tm_graph* g, const tm_query& q) {
@@ -71,6 +93,7 @@ void worker_main(tm_server* S) {
     for (;;) {
         int32_t gid = -1;
         int64_t fp_total = 0;
+        double work = 0.0, budget = 0.0;
         ids.clear();
         qs.clear();
         {
@@ -92,6 +115,12 @@ void worker_main(tm_server* S) {
                             continue;
                         }
                         if (S->in_use + fp_total + T.footprint > S->cfg.mem_budget_bytes) break;
+                        // the oldest query always goes; later ones join while the batch's
+                        // predicted work stays within twice the oldest's (and a floor), so a
+                        // heavy query does not hold many light ones back
+                        if (!ids.empty() && work + T.pred > budget) { ++it; continue; }
+                        if (ids.empty()) budget = std::max(2.0 * T.pred, kWorkFloor);
+                        work += T.pred;
                         gid = T.gid;
                         fp_total += T.footprint;
                         T.state = kRunning;
@@ -118,6 +147,12 @@ void worker_main(tm_server* S) {
                 Ticket& T = it->second;
                 T.state = kDone;
                 T.r = rs[i];
+                if (rs[i].status == TM_OK) {
+                    double w = (double)rs[i].first_edges + (double)rs[i].cand_edges + (double)rs[i].inst_read;
+                    auto e = S->work_ema.find(T.cls);
+                    if (e == S->work_ema.end()) S->work_ema.emplace(T.cls, w);
+                    else e->second = 0.5 * e->second + 0.5 * w;
+                }
                 if (rc != TM_OK && rs[i].status == TM_OK && rc != TM_EINVAL && rc != TM_EOVERFLOW) {
                     T.r.status = rc;  // batch-level failure (CUDA, memory)
                 }
@@ -184,6 +219,10 @@ int tm_serve_submit(tm_server* S, int32_t graph_id, const tm_query* q, uint64_t*
     T.gid = graph_id;
     T.q = *q;
     T.footprint = footprint(S->graphs[(size_t)graph_id], *q);
+    T.cls = class_key(graph_id, *q);
+    auto e = S->work_ema.find(T.cls);
+    // unseen classes are assumed heavy (four reads per edge of the graph) until measured
+    T.pred = e != S->work_ema.end() ? e->second : 4.0 * (double)S->graphs[(size_t)graph_id]->m;
     S->tickets.emplace(id, T);
     S->queue.push_back(id);
     *ticket = id;

@@ -220,6 +220,7 @@ int sm_count();
 // per device; pool_free returns a stream-ordered block on an internal stream
 int pool_prepare(int dev);
 void pool_free(void* p, int dev);
+int pool_trim();
 
 // profiling (abi.cu): phase events of the last batch / graph build, launch counter
 bool profiling();

@@ -243,3 +243,117 @@ MOTIFS = {
     "pingpong": ([0, 1, 0], [1, 0, 1]),        # a->b, b->a, a->b
     "cycle4": ([0, 1, 2, 3], [1, 2, 3, 0]),    # a->b, b->c, c->d, d->a
 }
+
+
+def chung_lu_hawkes_gpu(n_nodes: int, m_edges: int, gamma: float, seed: int,
+                        horizon: int = TWO_YEARS_S, branching: float = 0.5,
+                        kernel_mean_s: float = 60.0, i0: float = 1.0,
+                        max_degree: int | None = None, hub_bursts: int = 0,
+                        burst_max: int = 10_000, burst_window_s: float = 60.0,
+                        device: str = "cuda"):
+    """The same recipe as chung_lu_hawkes, drawn with torch on a CUDA device
+    (seeded torch generator) for graphs too large to draw in numpy: returns
+    time-sorted (src int32, dst int32, t int64) device tensors.  Its random
+    stream differs from the numpy generator's."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    cap = None if max_degree is None else max_degree / float(m_edges)
+    w = _power_weights(n_nodes, gamma, i0, cap)
+    cdf = torch.from_numpy(np.cumsum(w) / np.sum(w)).to(device)
+    perm_out = torch.randperm(n_nodes, generator=gen, device=device).to(torch.int32)
+    perm_in = torch.randperm(n_nodes, generator=gen, device=device).to(torch.int32)
+
+    def draw(perm, k):
+        u = torch.rand(k, generator=gen, device=device, dtype=torch.float64)
+        idx = torch.searchsorted(cdf, u, right=True).clamp_(max=n_nodes - 1)
+        return perm[idx]
+
+    def fix_loops(s, d):
+        bad = s == d
+        nb = int(bad.sum())
+        while nb:
+            d[bad] = draw(perm_in, nb)
+            bad = s == d
+            nb = int(bad.sum())
+        return d
+
+    n_b_total = 0
+    bursts = []
+    if hub_bursts > 0:
+        hubs = perm_out[torch.from_numpy(np.argsort(-w)[: max(1, min(hub_bursts, 64))].copy()).to(device)]
+        rs = np.random.default_rng(seed)
+        for b in range(hub_bursts):
+            size = int(rs.integers(burst_max // 2, burst_max + 1))
+            start = rs.random() * (horizon - burst_window_s)
+            bt = torch.floor(start + torch.rand(size, generator=gen, device=device, dtype=torch.float64)
+                             * burst_window_s)
+            bs = torch.full((size,), int(hubs[b % len(hubs)]), dtype=torch.int32, device=device)
+            bd = fix_loops(bs, draw(perm_in, size))
+            bursts.append((bs, bd, bt))
+            n_b_total += size
+    m_base = max(m_edges - n_b_total, 0)
+
+    srcs, dsts, ts = [], [], []
+    total = 0
+    target = int(m_base * 1.03) + 64
+    rs = np.random.default_rng(seed + 1)
+    while total < m_base:
+        n_imm = int(rs.poisson((1.0 - branching) * target))
+        t_par = torch.rand(n_imm, generator=gen, device=device, dtype=torch.float64) * horizon
+        s_par = draw(perm_out, n_imm)
+        d_par = fix_loops(s_par, draw(perm_in, n_imm))
+        gs_, gd_, gt_ = [s_par], [d_par], [t_par]
+        while t_par.numel():
+            rate = torch.full((t_par.numel(),), branching, device=device, dtype=torch.float64)
+            kids = torch.poisson(rate, generator=gen).to(torch.int64)
+            n_k = int(kids.sum())
+            if n_k == 0:
+                break
+            rep = torch.repeat_interleave(torch.arange(t_par.numel(), device=device), kids)
+            delay = torch.empty(n_k, device=device, dtype=torch.float64).exponential_(1.0 / kernel_mean_s,
+                                                                                    generator=gen)
+            t_c = t_par[rep] + delay
+            reply = torch.rand(n_k, generator=gen, device=device) < 0.5
+            s_c = torch.where(reply, d_par[rep], s_par[rep])
+            d_c = torch.where(reply, s_par[rep], draw(perm_in, n_k))
+            d_c = fix_loops(s_c, d_c)
+            keep = t_c < horizon
+            t_par, s_par, d_par = t_c[keep], s_c[keep], d_c[keep]
+            gs_.append(s_par)
+            gd_.append(d_par)
+            gt_.append(t_par)
+        s_all, d_all, t_all = torch.cat(gs_), torch.cat(gd_), torch.cat(gt_)
+        del gs_, gd_, gt_
+        srcs.append(s_all)
+        dsts.append(d_all)
+        ts.append(t_all)
+        total += t_all.numel()
+        target = max(m_base - total, 0) + 64
+    t = torch.floor(torch.cat(ts)).to(torch.int64)
+    src = torch.cat(srcs)
+    dst = torch.cat(dsts)
+    del srcs, dsts, ts
+    # earliest m_base background events, then the bursts, all sorted by time (stable)
+    order = torch.sort(t, stable=True).indices[:m_base]
+    src, dst, t = src[order], dst[order], t[order]
+    del order
+    if bursts:
+        src = torch.cat([src] + [b[0] for b in bursts])
+        dst = torch.cat([dst] + [b[1] for b in bursts])
+        t = torch.cat([t] + [b[2].to(torch.int64) for b in bursts])
+        order = torch.sort(t, stable=True).indices
+        src, dst, t = src[order], dst[order], t[order]
+        del order
+    src, dst, t = src.contiguous(), dst.contiguous(), t.contiguous()
+    torch.cuda.empty_cache()   # hand the generator's scratch back before the graph is built
+    return src, dst, t
+
+
+def config5_graph_gpu(seed: int = 5, m_edges: int = 1_000_000_000, n_nodes: int = 10_000_000,
+                      device: str = "cuda"):
+    """N=1e7, M=1e9, Chung-Lu exponent 1.8 with the maximum expected degree
+    capped at 5e6, Hawkes times over two years, and 1,000 hub bursts of up to
+    1e4 edges within 60 s; drawn on the GPU."""
+    return chung_lu_hawkes_gpu(n_nodes, m_edges, 1.8, seed, max_degree=5_000_000, hub_bursts=1000,
+                               burst_max=10_000, device=device)

@@ -102,6 +102,7 @@ _SIGS = {
     "tm_autotune": (ctypes.c_int, [_vp, _vp, _c_i32, _vp]),
     "tm_profile_enable": (ctypes.c_int, [_c_i32]),
     "tm_profile_last": (ctypes.c_int, [_vp]),
+    "tm_release_cached_memory": (ctypes.c_int, []),
     "tm_serve_create": (ctypes.c_int, [_vp, _vp]),
     "tm_serve_attach_graph": (ctypes.c_int, [_vp, _vp, _vp]),
     "tm_serve_submit": (ctypes.c_int, [_vp, _c_i32, _vp, _vp]),
@@ -400,6 +401,10 @@ def profile_last() -> dict:
     p = ProfileC()
     _check(lib().tm_profile_last(ctypes.byref(p)), "tm_profile_last")
     return {f: getattr(p, f) for f, _ in ProfileC._fields_}
+
+
+def release_cached_memory():
+    _check(lib().tm_release_cached_memory(), "tm_release_cached_memory")
 
 
 class Server:

@@ -378,3 +378,103 @@ def test_wide_time_span_uses_64_bit_times(tm, orc):
             d2, c2, p2 = est
             z = tm.estimate(g, mo, d2, c2, p2, 17)
             assert _close(z, orc.estimate(src, dst, t, ms, md, d2, c2, p2, 17))
+
+
+@pytest.mark.slow
+def test_config3_full_size_sampled_windows(tm, orc):
+    """Config 3 size (N=1e6, M=1e8, Chung-Lu 2.0 + Hawkes): the 4-cycle at
+    delta=3600 in the batched launch the benchmark times (all c x p x seed
+    combinations of one shift each in one batch); per-window exact counts and
+    weights of sampled kept windows checked one by one against the oracle."""
+    import torch
+    src, dst, t = synth.config3_graph()
+    g = _graph(tm, src, dst, t)
+    tn = t - t.min()
+    ms, md = synth.MOTIFS["cycle4"]
+    mo = tm.Motif(ms, md)
+    qs = [tm.estimate_query(mo, 3600, c, p, seed=9000 + s) for c in (10, 30, 100) for p in (0.01, 0.1)
+          for s in range(4)]
+    res = tm.run_batch(g, qs)
+    assert all(r["status"] == 0 for r in res)
+    rng = np.random.default_rng(3)
+    for (c, p, seed) in ((10, 0.01, 9000), (100, 0.1, 9002)):
+        shift, recs = tm.estimate_windows(g, mo, 3600, c, p, seed)
+        nz = [r for r in recs if r["hi"] > r["lo"]]
+        cd = c * 3600
+        for i in rng.choice(len(nz), size=min(3, len(nz)), replace=False):
+            r = nz[int(i)]
+            lo, hi = r["lo"], r["hi"]
+            cnt, hist, _ = orc.count_exact_hist(src[lo:hi], dst[lo:hi], tn[lo:hi], ms, md, 3600,
+                                                threads=16, n_nodes=1_000_000)
+            assert r["count"] == cnt
+            wo = math.fsum((int(hist[d]) * cd) / (cd - d) for d in np.nonzero(hist)[0])
+            w = r["w_int"] + r["w_frac"] * 2.0 ** -64
+            assert abs(w - wo) <= EST_RTOL * wo + cnt * 2.0 ** -64
+        # the single-query estimate equals the batched one for the same seed
+        z = tm.estimate(g, mo, 3600, c, p, seed)
+        k = [i for i, q in enumerate(qs) if (q.c, q.p, q.seed) == (c, p, seed)][0]
+        assert z == res[k]["estimate"]
+
+
+@pytest.mark.slow
+def test_config5_full_size_sampled_windows(tm, orc):
+    """Config 5 size (N=1e7, M=1e9, Chung-Lu 1.8 capped at degree 5e6, Hawkes
+    times plus 1,000 hub bursts of up to 1e4 edges in 60 s), drawn on the GPU:
+    the out-star at delta=1800 estimated with c=30, p=0.01 for 8 seeds in one
+    batched launch; sampled kept windows checked one by one against the oracle.
+    Windows holding a hub burst are not sampled (the oracle's enumeration is
+    cubic in a burst; bursts are checked at smaller scale in test_hub_heavy_graph)."""
+    import torch
+    d_src, d_dst, d_t = synth.config5_graph_gpu()
+    g = tm.Graph(d_src, d_dst, d_t)
+    ms, md = synth.MOTIFS["outstar3"]
+    mo = tm.Motif(ms, md)
+    res = tm.run_batch(g, [tm.estimate_query(mo, 1800, 30, 0.01, seed=500 + s) for s in range(8)])
+    assert all(r["status"] == 0 and r["windows_kept"] > 0 for r in res)
+    # per-window detail at p = 0.1 (about 117 kept windows, some 40 % of them burst-free)
+    shift, recs = tm.estimate_windows(g, mo, 1800, 30, 0.1, 500)
+    t_min = int(d_t[0])
+    cd = 30 * 1800
+    checked = 0
+    for r in recs:
+        if checked == 3:
+            break
+        lo, hi = r["lo"], r["hi"]
+        if hi <= lo:
+            continue
+        src = d_src[lo:hi].cpu().numpy()
+        tn = d_t[lo:hi].cpu().numpy() - t_min
+        # a hub burst: one source with > 1,000 edges in one 10-minute bin
+        # (the heaviest hubs average about 50 per bin)
+        binned = src.astype(np.int64) * (1 << 20) + (tn - tn.min()) // 600
+        if np.unique(binned, return_counts=True)[1].max() > 1000:
+            continue
+        dst = d_dst[lo:hi].cpu().numpy()
+        cnt, hist, _ = orc.count_exact_hist(src, dst, tn, ms, md, 1800, threads=16, n_nodes=10_000_000)
+        assert r["count"] == cnt
+        wo = math.fsum((int(hist[d]) * cd) / (cd - d) for d in np.nonzero(hist)[0])
+        w = r["w_int"] + r["w_frac"] * 2.0 ** -64
+        assert abs(w - wo) <= EST_RTOL * wo + cnt * 2.0 ** -64
+        checked += 1
+    assert checked >= 2
+    g.free()
+    del d_src, d_dst, d_t
+    torch.cuda.empty_cache()
+    tm.release_cached_memory()
+
+
+def test_dense_sampling_node_grouped_windows(tm, orc):
+    """Estimates that keep most windows, with windows holding many edges per
+    node, enumerate each window's first edges grouped by node (a per-shift
+    partition of the adjacency view by window); same results as the oracle,
+    window by window."""
+    src, dst, t = synth.chung_lu_hawkes(200, 50_000, 2.1, seed=27, horizon=1_000_000)
+    g = _graph(tm, src, dst, t)
+    for name in ("cycle3", "outstar3", "pingpong", "cycle4"):
+        ms, md = synth.MOTIFS[name]
+        mo = tm.Motif(ms, md)
+        for (c, p, seed, b) in ((10, 0.3, 1, 2), (10, 1.0, 2, 1), (30, 0.6, 3, 1)):
+            r = tm.run_batch(g, [tm.estimate_query(mo, 3600, c, p, seed, b=b)])[0]
+            zo = orc.estimate(src, dst, t, ms, md, 3600, c, p, seed, b=b, threads=8)
+            assert _close(r["estimate"], zo), (name, c, p, seed, b, r["estimate"], zo)
+        _check_windows(tm, orc, g, src, dst, t, ms, md, 3600, 10, 0.5, 4)
