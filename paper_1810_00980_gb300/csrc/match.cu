@@ -78,6 +78,9 @@ struct MatchArgs {
     unsigned long long* counter;
     int64_t chunk;
     int enum_threshold;
+    const int32_t* blockwin = nullptr;  // [ceil(F/32)] window of first edge 32 b (null: searched)
+    const int64_t* chunkf = nullptr;    // [nchunkf] first edge of work item i * chunk (null: searched)
+    int64_t nchunkf = 0;
 };
 
 // ----------------------------------------------------------------- helpers
@@ -479,6 +482,35 @@ __global__ void k_woff(const uint32_t* __restrict__ keys, int64_t m, int64_t nke
     }
 }
 
+// window of first edge 32 b for every block b of 32 first edges: one search each,
+// run at full occupancy instead of on the critical path of k_level2's warps
+__global__ void k_blockwin(const int64_t* __restrict__ fbase, int64_t NW, int64_t Fh,
+                           const int64_t* __restrict__ d_F, int32_t* __restrict__ bw) {
+    const int64_t F = d_F ? *d_F : Fh;
+    int64_t nb = (F + 31) >> 5;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = b << 5, lo = 0, hi = NW;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (__ldg(fbase + mid) <= x) lo = mid; else hi = mid;
+        }
+        bw[b] = (int32_t)lo;
+    }
+}
+
+// first edge of work item i * chunk (the start of k_match's i-th chunk), for the first
+// cap chunks and the one after the last
+__global__ void k_chunkf(const int64_t* __restrict__ excl, int64_t Fh, const int64_t* __restrict__ d_F,
+                         const int64_t* __restrict__ d_W2, int64_t chunk, int64_t cap,
+                         int64_t* __restrict__ cf) {
+    const int64_t F = d_F ? *d_F : Fh;
+    int64_t n = min(cap, (*d_W2 + chunk - 1) / chunk + 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        cf[i] = upper_bound_i64(excl, 0, F, i * chunk) - 1;
+}
+
 // one warp-uniform grid-stride loop over first edges f
 template <typename TT>
 __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __restrict__ fwin,
@@ -498,22 +530,33 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
         int64_t f = base + lane;
         bool valid = f < F;
         int64_t wi = -1;
-        // window of the warp's first edge by one binary search; lanes past its end search on
+        // window of the warp's first edge (precomputed per 32 first edges, else one binary
+        // search); lanes past its end gallop forward from it
         int64_t w0 = 0;
-        if (lane == 0) {
-            int64_t lo = 0, hi = A.NW;
-            while (hi - lo > 1) {
-                int64_t mid = (lo + hi) >> 1;
-                if (__ldg(A.W.fbase + mid) <= base) lo = mid; else hi = mid;
+        if (A.blockwin) {
+            w0 = __ldg(A.blockwin + (base >> 5));
+        } else {
+            if (lane == 0) {
+                int64_t lo = 0, hi = A.NW;
+                while (hi - lo > 1) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (__ldg(A.W.fbase + mid) <= base) lo = mid; else hi = mid;
+                }
+                w0 = lo;
             }
-            w0 = lo;
+            w0 = __shfl_sync(kFull, w0, 0);
         }
-        w0 = __shfl_sync(kFull, w0, 0);
         if (valid) {
             if (f < __ldg(A.W.fbase + w0) + __ldg(A.W.nfirst + w0)) {
                 wi = w0;
             } else {
                 int64_t lo = w0, hi = A.NW;   // last window whose fbase <= f
+                for (int64_t step = 1;; step <<= 1) {
+                    int64_t nx = lo + step;
+                    if (nx >= A.NW) break;
+                    if (__ldg(A.W.fbase + nx) > f) { hi = nx; break; }
+                    lo = nx;
+                }
                 while (hi - lo > 1) {
                     int64_t mid = (lo + hi) >> 1;
                     if (__ldg(A.W.fbase + mid) <= f) lo = mid; else hi = mid;
@@ -793,12 +836,20 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
         if (c0 >= W2) break;
         int64_t c1 = min(c0 + A.chunk, W2);
         int64_t fb = 0, fe = 0;
-        if (lane < 2) {
-            int64_t key = lane == 0 ? c0 : c1 - 1;
-            fb = upper_bound_i64(A.excl, 0, F, key) - 1;
+        int64_t ci = c0 / A.chunk;
+        if (A.chunkf && ci + 1 < A.nchunkf) {
+            // first edges of this chunk's first item and of the next chunk's (a bound on
+            // the last item's: first edges in between have no items below c1)
+            fb = __ldg(A.chunkf + ci);
+            fe = __ldg(A.chunkf + ci + 1);
+        } else {
+            if (lane < 2) {
+                int64_t key = lane == 0 ? c0 : c1 - 1;
+                fb = upper_bound_i64(A.excl, 0, F, key) - 1;
+            }
+            fe = __shfl_sync(kFull, fb, 1);
+            fb = __shfl_sync(kFull, fb, 0);
         }
-        fe = __shfl_sync(kFull, fb, 1);
-        fb = __shfl_sync(kFull, fb, 0);
         int64_t fcur = fb;   // first edge of the round's first item
         for (int64_t base = c0; base < c1; base += 32) {
             int64_t w = base + lane;
@@ -1311,7 +1362,9 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     char* fb = nullptr;
     if (rc == TM_OK && F > 0) {
         size_t Fs = (size_t)F;
-        fail(cudaMallocAsync((void**)&fb, a256(4 * Fs) + (any_hoist ? 5 : 3) * a256(8 * Fs), st),
+        size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
+        fail(cudaMallocAsync((void**)&fb, a256(4 * Fs) + (any_hoist ? 5 : 3) * a256(8 * Fs) + a256(4 * nbw) +
+                                              a256(8 * ncf), st),
              "per-edge scratch");
         if (rc == TM_OK) {
             char* q2 = fb;
@@ -1321,22 +1374,34 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             int64_t* excl = (int64_t*)take2(8 * Fs);   // range lengths, then their exclusive scan in place
             int64_t* hs_a = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             int64_t* hs_hi = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
+            int32_t* bwin = (int32_t*)take2(4 * nbw);
+            int64_t* cf = (int64_t*)take2(8 * ncf);
             MatchArgs<TT> A;
             A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = F; A.d_F = nullptr;
             A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
             A.d_W2 = dW2; A.counter = dctr;
             A.enum_threshold = tu.enum_threshold;
+            A.chunk = tu.chunk_items;
+            A.blockwin = bwin; A.chunkf = cf; A.nchunkf = (int64_t)ncf;
             int bt = tu.block_threads;
             int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
+            k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
+                W.fbase, NW, F, nullptr, bwin);
+            count_launch();
             ev_l0 = pe.mark(st);
             k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
             fail(cudaGetLastError(), "k_level2");
             ev_l2 = pe.mark(st);
             if (rc == TM_OK) rc = scan_exclusive_i64(excl, excl, F, dW2, st);
+            if (rc == TM_OK) {
+                k_chunkf<<<(unsigned)std::min<int64_t>(((int64_t)ncf + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
+                    excl, F, nullptr, dW2, A.chunk, (int64_t)ncf, cf);
+                count_launch();
+                fail(cudaGetLastError(), "k_chunkf");
+            }
             ev_l1 = pe.mark(st);
             if (rc == TM_OK) {
                 int bps = tu.blocks_per_sm;
-                A.chunk = tu.chunk_items;
                 unsigned gm = (unsigned)(nsm * bps);
                 if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
                     k_match<TT, 3, 4, 6><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
@@ -1722,7 +1787,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     int64_t ws2 = scan_dn_ws_elems(Fmax) + 2;
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
-                a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2);
+                a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2) +
+                a256(4 * (Fs / 32 + 1)) + a256(8 * (Fs / 4 + 2));
     cudaError_t e = cudaMalloc(&b->scratch, sz);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_res, sizeof(tm_result) * (size_t)nq);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -1765,6 +1831,9 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     int64_t* hs_hi = any_hoist ? (int64_t*)take(8 * Fs) : nullptr;
     int64_t* wsp1 = (int64_t*)take(8 * (size_t)ws1);
     int64_t* wsp2 = (int64_t*)take(8 * (size_t)ws2);
+    size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
+    int32_t* bwin = (int32_t*)take(4 * nbw);
+    int64_t* cf = (int64_t*)take(8 * ncf);
 
     cudaStream_t st = b->cap;
     int rc = TM_OK;
@@ -1807,10 +1876,20 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         A.d_W2 = dW2; A.counter = dctr;
         A.enum_threshold = tu.enum_threshold;
         A.chunk = tu.chunk_items;
+        A.blockwin = bwin; A.chunkf = cf; A.nchunkf = (int64_t)ncf;
         int64_t gl2 = std::min<int64_t>((Fmax + 255) / 256, (int64_t)nsm * 8);
+        k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
+            W.fbase, NW, Fmax, dF, bwin);
+        count_launch();
         k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
         fail(cudaGetLastError(), "k_level2");
         if (rc == TM_OK) rc = scan_exclusive_i64_dn(excl, excl, Fmax, dF, dW2, wsp2, ws2, st);
+        if (rc == TM_OK) {
+            k_chunkf<<<(unsigned)std::min<int64_t>(((int64_t)ncf + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
+                excl, Fmax, dF, dW2, A.chunk, (int64_t)ncf, cf);
+            count_launch();
+            fail(cudaGetLastError(), "k_chunkf");
+        }
         if (rc == TM_OK) {
             unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
             int bt = tu.block_threads;
