@@ -5,6 +5,7 @@
 // segment offsets found from the sorted keys.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "tm_internal.cuh"
 
@@ -272,6 +273,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     G.out_src = out_src; G.in_dst = in_dst; G.pair_pid = pair_pid;
     G.hslots = nullptr; G.hmask = 0;
     g->hash_block = nullptr;
+    g->ex_own_block = nullptr;
+    g->ex_rev_block = nullptr;
 
     int rc = TM_OK;
     if (m == 0) {
@@ -410,7 +413,77 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     return TM_OK;
 }
 
+// Two-node tables.  For pair-view position e of pair (u, v) at time t_e:
+//   own[e] = number of (u, v) edges with time < t_e, rev[e] = number of (v, u) edges with
+//   time < t_e;
+// each then turned into exclusive prefix sums over all positions.  The source of pair-view
+// position e is out_src[e]: both views group the edges by source in the same ranges.
+template <typename TT>
+__global__ void k_ex_rank(GraphDevT<TT> G, int reverse, int64_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < G.m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t pid = G.pair_pid[e];
+        int64_t te = (int64_t)G.pair_t[e];
+        if (!reverse) {
+            int64_t pa = G.pair_off[pid];
+            int64_t r = e - pa;
+            if (e > pa && (int64_t)G.pair_t[e - 1] == te) r = lower_bound_i64(G.pair_t, pa, e, te) - pa;
+            out[e] = r;
+        } else {
+            int32_t u = G.out_src[e], v = G.pair_dst[pid];
+            int64_t ra, rb;
+            out[e] = pair_segment(G, v, u, ra, rb) ? lower_bound_i64(G.pair_t, ra, rb, te) - ra : 0;
+        }
+    }
+}
+
+std::mutex g_ex_mu;
+
+int build_ex_table(tm_graph* g, int reverse, cudaStream_t st, void** blk_out) {
+    size_t n1 = (size_t)g->m + 1;
+    void* blk = nullptr;
+    TM_CUDA(cudaMallocAsync(&blk, align256(8 * n1), st));
+    int64_t* a = (int64_t*)blk;
+    int rc = TM_OK;
+    cudaError_t e = cudaMemsetAsync(a + g->m, 0, 8, st);
+    if (e == cudaSuccess) {
+        if (g->dev.tbytes == 4) k_ex_rank<int32_t><<<grid_for(g->m), kThreads, 0, st>>>(typed<int32_t>(g->dev), reverse, a);
+        else k_ex_rank<int64_t><<<grid_for(g->m), kThreads, 0, st>>>(typed<int64_t>(g->dev), reverse, a);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) rc = cuda_status(e, "two-node table", __FILE__, __LINE__);
+    if (rc == TM_OK) rc = scan_exclusive_i64(a, a, (int64_t)n1, nullptr, st);
+    if (rc == TM_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_status(e, "two-node table", __FILE__, __LINE__);
+    }
+    if (rc != TM_OK) {
+        cudaStreamSynchronize(st);
+        pool_free(blk, g->device);
+        return rc;
+    }
+    g->bytes += (int64_t)align256(8 * n1);
+    *blk_out = blk;
+    return TM_OK;
+}
+
 }  // namespace
+
+int ensure_ex_tables(tm_graph* g, cudaStream_t st, bool need_own, bool need_rev, const int64_t** own,
+                     const int64_t** rev) {
+    std::lock_guard<std::mutex> lk(g_ex_mu);
+    *own = *rev = nullptr;
+    if (g->m == 0) return TM_OK;
+    int rc = TM_OK;
+    if (need_own && !g->ex_own_block) rc = build_ex_table(g, 0, st, &g->ex_own_block);
+    if (rc == TM_OK && need_rev && !g->ex_rev_block) rc = build_ex_table(g, 1, st, &g->ex_rev_block);
+    if (rc != TM_OK) return rc;
+    if (need_own) *own = (const int64_t*)g->ex_own_block;
+    if (need_rev) *rev = (const int64_t*)g->ex_rev_block;
+    return TM_OK;
+}
+
 }  // namespace tmo
 
 extern "C" {
@@ -452,6 +525,8 @@ void tm_graph_free(tm_graph* g) {
     if (!g) return;
     tmo::pool_free(g->block, g->device);
     tmo::pool_free(g->hash_block, g->device);
+    tmo::pool_free(g->ex_own_block, g->device);
+    tmo::pool_free(g->ex_rev_block, g->device);
     delete g;
 }
 

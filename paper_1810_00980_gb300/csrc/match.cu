@@ -124,26 +124,6 @@ __device__ __forceinline__ int64_t gallop_ub(const T* __restrict__ a, int64_t lo
 // time-sorted entries of the (u -> v) pair: [a, b) of pair_t, through the
 // open-addressing hash of static edges (probe chains end at an empty slot)
 template <typename TT>
-__device__ __forceinline__ bool pair_segment(const GraphDevT<TT>& G, int32_t u, int32_t v, int64_t& a,
-                                             int64_t& b) {
-    unsigned long long key = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
-    unsigned long long h = sm64_mix(key) & G.hmask;
-    for (unsigned long long it = 0; it <= G.hmask; it++) {
-        ulonglong2 sl = __ldg(reinterpret_cast<const ulonglong2*>(G.hslots) + h);
-        if (sl.x == key) {
-            a = (int64_t)(uint32_t)sl.y;
-            b = a + (int64_t)(sl.y >> 32);
-            return true;
-        }
-        unsigned long long k = sl.x;
-        if (k == kHashEmpty) break;
-        h = (h + 1) & G.hmask;
-    }
-    a = b = 0;
-    return false;
-}
-
-template <typename TT>
 __device__ __forceinline__ int64_t pair_count(const GraphDevT<TT>& G, int32_t u, int32_t v, int64_t tprev,
                                               int64_t thi) {
     int64_t a, b;
@@ -583,6 +563,46 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
             if (Q.l == 1) {
                 acc.f[A_COUNT] += 1;
                 if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, 0);
+            } else if (Q.ex23) {
+                // two-node motif (Algorithm 2): for a last edge j in (t1, thi] the middle
+                // edges are those of the middle pair with time in (t1, t_j), a difference of
+                // two counts; exact counts sum it over j in O(1) from the prefix tables.
+                // The last edges' range comes first: most first edges have none.
+                const bool mid_rev = Q.ex23 & kEx23MidRev, last_rev = Q.ex23 & kEx23LastRev;
+                int64_t pa = 0, pb = 0, own_ub = 0, ra = 0, rb = 0, rev_ub = 0;
+                bool have_own = false, have_rev = false;
+                auto own_side = [&]() {
+                    if (Q.order == kOrdPair) {
+                        int32_t pid = __ldg(G.pair_pid + e1);
+                        pa = __ldg(G.pair_off + pid);
+                        pb = __ldg(G.pair_off + pid + 1);
+                        own_ub = gallop_ub(G.pair_t, e1 + 1, pb, t1);
+                    } else {
+                        pair_segment(G, s1, d1, pa, pb);   // e1 is one of the pair's edges
+                        own_ub = upper_bound_i64(G.pair_t, pa, pb, t1);
+                    }
+                    have_own = true;
+                };
+                auto rev_side = [&]() {
+                    if (pair_segment(G, d1, s1, ra, rb)) rev_ub = upper_bound_i64(G.pair_t, ra, rb, t1);
+                    have_rev = true;
+                };
+                if (last_rev) rev_side(); else own_side();
+                ha = last_rev ? rev_ub : own_ub;
+                hh = thi > t1 ? gallop_ub(G.pair_t, ha, last_rev ? rb : pb, thi) : ha;
+                if (hh > ha) {
+                    if (mid_rev && !have_rev) rev_side();
+                    if (!mid_rev && !have_own) own_side();
+                    int64_t le2 = mid_rev ? rev_ub - ra : own_ub - pa;   // middle-pair edges at or before t1
+                    if (Q.mode == TM_MODE_EXACT) {
+                        const int64_t* S = mid_rev == last_rev ? G.ex_own : G.ex_rev;
+                        acc.f[A_COUNT] += (unsigned long long)((__ldg(S + hh) - __ldg(S + ha)) - (hh - ha) * le2);
+                        acc.f[A_LAST] += 1;
+                    } else {
+                        len = hh - ha;   // items: the last edges; k_match reads ha and le2
+                        hh = le2;
+                    }
+                }
             } else {
                 int32_t phi[2] = {s1, d1};
                 const LevelPlan P = Q.lv[1];
@@ -883,7 +903,22 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                 first_edge(G, Q.order, e1, phi[0], phi[1], t1);
                 thi = min(t1 + Q.delta, A.W.tend[win]);
                 int64_t l2 = A.lo2[f];
-                if (l2 < 0 && Q.hoist) {
+                if (Q.ex23) {
+                    // two-node motif: item = last edge j; its middle edges number
+                    // (middle-pair edges before t_j) - (those at or before t1)
+                    const bool mid_rev = Q.ex23 & kEx23MidRev, last_rev = Q.ex23 & kEx23LastRev;
+                    const int64_t* S = mid_rev == last_rev ? G.ex_own : G.ex_rev;
+                    int64_t j = A.hs_a[f] + (w - A.excl[f]);
+                    int64_t t3 = __ldg(G.pair_t + j);
+                    int64_t cnt = (__ldg(S + j + 1) - __ldg(S + j)) - A.hs_hi[f];
+                    acc_switch(acc, win, A.W.acc);
+                    acc.f[A_CAND] += 1;
+                    acc.f[A_LAST] += 1;
+                    if (cnt > 0) {
+                        acc.f[A_COUNT] += cnt;
+                        if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                    }
+                } else if (l2 < 0 && Q.hoist) {
                     // closing edge e3 of the first edge's pair: count the valid second
                     // edges with time in (t1, t3)
                     const LevelPlan L = Q.lv[2];
@@ -1178,9 +1213,15 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
         bool closes_x = L2.view == kPair && ((L2.su == 2 && L2.sv <= 1) || (L2.sv == 2 && L2.su <= 1));
         P.rev = (one_new && closes_x) ? 1 : 0;
     }
+    // two nodes, three edges (Algorithm 2's motif family): counted from the pair tables
+    P.ex23 = 0;
+    if (m->k == 2 && m->l == 3 && m->lv[1].su != m->lv[1].sv && m->lv[2].su != m->lv[2].sv) {
+        P.ex23 = kEx23On | (m->lv[1].su == 1 ? kEx23MidRev : 0) | (m->lv[2].su == 1 ? kEx23LastRev : 0);
+        P.hoist = P.hrev = P.rev = P.rev2 = 0;
+    }
     // when the closing edge repeats the first edge's pair, first edges go in pair order:
     // the closing range then starts right after the first edge's own position
-    bool own_pair = P.hoist && m->lv[m->l - 1].su == 0 && m->lv[m->l - 1].sv == 1;
+    bool own_pair = (P.hoist && m->lv[m->l - 1].su == 0 && m->lv[m->l - 1].sv == 1) || P.ex23;
     if (q.mode == TM_MODE_EXACT) {
         P.b = 1; P.cd = 0; P.J = 1; P.p = 1.0; P.q_mode = TM_Q_UNIFORM;
         // exact queries take first edges grouped by the node their second edge hangs off
@@ -1220,6 +1261,21 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
 
 }  // namespace
 
+// the two-node tables the batch's two-node queries read: own when the middle and the last
+// edge are on the same pair, rev otherwise
+template <typename TT>
+int ex_tables_for(const tm_graph* g, const std::vector<QPlan>& hp, cudaStream_t st, GraphDevT<TT>& G) {
+    bool need_own = false, need_rev = false;
+    for (const QPlan& P : hp) {
+        if (!P.ex23) continue;
+        bool same = ((P.ex23 & kEx23MidRev) != 0) == ((P.ex23 & kEx23LastRev) != 0);
+        need_own |= same;
+        need_rev |= !same;
+    }
+    if (!need_own && !need_rev) return TM_OK;
+    return ensure_ex_tables(const_cast<tm_graph*>(g), st, need_own, need_rev, &G.ex_own, &G.ex_rev);
+}
+
 template <typename TT>
 int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
                 BatchOut* dbg) {
@@ -1250,7 +1306,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         NW += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].J * hp[(size_t)i].b;
         lmax = std::max(lmax, hp[(size_t)i].l);
         kmax = std::max(kmax, hp[(size_t)i].k);
-        any_hoist |= hp[(size_t)i].hoist != 0;
+        any_hoist |= hp[(size_t)i].hoist != 0 || hp[(size_t)i].ex23 != 0;
         if (hp[(size_t)i].mode == TM_MODE_ESTIMATE && hp[(size_t)i].delta + 1 <= kWtabMax)
             wtab_bytes += a256(16 * (size_t)(hp[(size_t)i].delta + 1));
         if (hp[(size_t)i].full) {
@@ -1324,6 +1380,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         }
     }
     GraphDevT<TT> G = typed<TT>(g->dev);
+    if (rc == TM_OK) rc = ex_tables_for(g, hp, st, G);
     int nsm = sm_count();
     // dense-sampling queries: per shift, node-grouped view positions stably partitioned by window
     for (int i = 0; i < nq && rc == TM_OK; i++) {
@@ -1648,6 +1705,7 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
     fill_plan(P, q, g);
     P.win_base = 0;
     P.hoist = 0;   // no per-first-edge closing ranges: keeps the scratch at its stated size
+    P.ex23 = 0;    // nor the two-node tables (an allocation)
     // every call starts from zeroed accumulators and queue counter
     cudaError_t e = cudaMemcpyAsync(dplan, &P, sizeof(P), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(W.acc, 0, 8 * A_N, st);
@@ -1779,7 +1837,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         Fmax += P.mode == TM_MODE_EXACT ? g->m : (int64_t)P.b * g->m;
         lmax = std::max(lmax, P.l);
         kmax = std::max(kmax, P.k);
-        any_hoist |= P.hoist != 0;
+        any_hoist |= P.hoist != 0 || P.ex23 != 0;
         if (P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) wtab_bytes += a256(16 * (size_t)(P.delta + 1));
     }
     size_t NWs = (size_t)std::max<int64_t>(NW, 1), Fs = (size_t)std::max<int64_t>(Fmax, 1);
@@ -1858,6 +1916,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     const Tuning tu = tuning();
     int nsm = sm_count();
     GraphDevT<TT> G = typed<TT>(g->dev);
+    if (rc == TM_OK) rc = ex_tables_for(g, hp, st, G);
+    if (rc != TM_OK) { batch_release(b); return rc; }
     tm_profile pr0;
     tm_profile_last(&pr0);
     fail(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");

@@ -87,6 +87,11 @@ struct GraphDevT {
     const unsigned long long* hslots;
     unsigned long long hmask;
     int32_t loops;
+    // two-node tables (set by the batch that needs them): over pair-view positions e,
+    // exclusive prefix sums of the number of edges of e's own pair (ex_own) and of its
+    // reverse pair (ex_rev) with time < t_e
+    const int64_t* ex_own;  // [m+1] or null
+    const int64_t* ex_rev;  // [m+1] or null
 };
 
 template <typename TT>
@@ -99,6 +104,7 @@ inline GraphDevT<TT> typed(const GraphDev& g) {
     r.pk_off = g.pk_off; r.pair_dst = g.pair_dst; r.pair_off = g.pair_off; r.pair_t = (const TT*)g.pair_t;
     r.out_src = g.out_src; r.in_dst = g.in_dst; r.pair_pid = g.pair_pid;
     r.hslots = g.hslots; r.hmask = g.hmask; r.loops = g.loops;
+    r.ex_own = nullptr; r.ex_rev = nullptr;
     return r;
 }
 
@@ -116,6 +122,8 @@ struct tm_graph {
     int64_t bytes;
     void* block;            // one device allocation holding every array
     void* hash_block;       // the (src, dst) -> pair index hash table
+    void* ex_own_block;     // the two-node tables ([m+1] each), built on first use (or null)
+    void* ex_rev_block;
     tmo::GraphDev dev;
 };
 
@@ -150,6 +158,10 @@ namespace tmo {
 // by source / destination (positions of the out / in view) for exact queries
 enum FirstOrder : int32_t { kOrdTime = 0, kOrdOut = 1, kOrdIn = 2, kOrdPair = 3 };
 
+// QPlan::ex23 bits: a motif on two nodes with three edges, (u,v) first; the middle and
+// the last edge each either repeat (u,v) or reverse it (v,u)
+enum Ex23Bits : int32_t { kEx23On = 1, kEx23MidRev = 2, kEx23LastRev = 4 };
+
 struct QPlan {
     int32_t l, k;
     int32_t mode;        // TM_MODE_*
@@ -165,7 +177,7 @@ struct QPlan {
     int32_t hrev;        // 1: three edges, closing pair fixed by the first edge, and the second
                          //    edge either joins the first edge's nodes or adds one node: the
                          //    closing pair's entries can be the items instead
-    int32_t pad2;
+    int32_t ex23;        // kEx23*: two-node three-edge motif counted from the pair tables
     const int32_t* perm; // [b*m] per shift: view positions stably partitioned by window
     const int64_t* woff; // [b*(J+1)] per shift: start of each window's positions in perm
     int64_t delta;
@@ -216,6 +228,11 @@ int scan_exclusive_i64_dn(const int64_t* in, int64_t* out, int64_t n_max, const 
                           int64_t* d_total, int64_t* ws, int64_t ws_elems, cudaStream_t st);
 
 int sm_count();
+// the graph's two-node tables (own, rev: [m+1] each) that are asked for, each built on
+// the first call that needs it (thread-safe; synchronises the stream when it builds);
+// null for an empty graph or when not asked for
+int ensure_ex_tables(tm_graph* g, cudaStream_t st, bool need_own, bool need_rev, const int64_t** own,
+                     const int64_t** rev);
 // device memory pool (prims.cu): raise the default pool's release threshold once
 // per device; pool_free returns a stream-ordered block on an internal stream
 int pool_prepare(int dev);
@@ -301,6 +318,27 @@ __host__ __device__ __forceinline__ uint64_t sm64_output(uint64_t seed, uint64_t
 // draw n of repetition k of a query seeded with `seed`
 __host__ __device__ __forceinline__ uint64_t draw(uint64_t seed, uint64_t k, uint64_t n) {
     return sm64_output(sm64_output(seed, k + 1), n + 1);
+}
+
+// the time-sorted segment [a, b) of pair (u, v) in the pair view, by one hash lookup
+template <typename TT>
+__device__ __forceinline__ bool pair_segment(const GraphDevT<TT>& G, int32_t u, int32_t v, int64_t& a,
+                                             int64_t& b) {
+    unsigned long long key = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
+    unsigned long long h = sm64_mix(key) & G.hmask;
+    for (unsigned long long it = 0; it <= G.hmask; it++) {
+        ulonglong2 sl = __ldg(reinterpret_cast<const ulonglong2*>(G.hslots) + h);
+        if (sl.x == key) {
+            a = (int64_t)(uint32_t)sl.y;
+            b = a + (int64_t)(sl.y >> 32);
+            return true;
+        }
+        unsigned long long k = sl.x;
+        if (k == kHashEmpty) break;
+        h = (h + 1) & G.hmask;
+    }
+    a = b = 0;
+    return false;
 }
 
 }  // namespace tmo
