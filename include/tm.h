@@ -207,6 +207,39 @@ int tm_run_batch(const tm_graph* g, const tm_query* queries, int32_t n_queries,
 int tm_count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, void* stream,
                            int64_t* count);
 
+/* ---- streaming (graphs held in host memory) -------------------------------------
+ * The sampling framework needs only the edges of one window at a time, so windows can
+ * be processed chronologically as the edges stream in (Section 4, the remark on
+ * streaming after the choice of q_j).  tm_stream_run evaluates a batch of queries over
+ * a time-sorted edge list in HOST memory without ever holding the whole graph on the
+ * device: the list is cut into chronological segments of about `segment_edges` edges
+ * (cut between distinct times; consecutive segments overlap by up to max(delta, 2 c
+ * delta) of time), each segment is copied to the device -- the copy of the next
+ * segment overlaps the matching of the current one -- and built into a graph; each
+ * estimate window is counted in the one segment that holds it whole, and each exact
+ * query's first edge in the one segment that holds its delta-span.  A segment grows
+ * past `segment_edges` when a single window or span holds more edges.
+ *   src, dst, t   host arrays of m edges, t sorted non-decreasingly (pinned memory is
+ *                 copied directly; pageable memory through pinned staging buffers)
+ *   n_nodes       node ids must lie in [0, n_nodes)
+ *   queries       as tm_run_batch; results[i] is identical to tm_run_batch's on the
+ *                 whole graph for counts and uniform-q estimates (the per-shift Q64
+ *                 weight sums add exactly); TM_Q_EDGES estimates and var_hat agree to
+ *                 rounding (their per-window terms are summed in another order)
+ *   stats         optional (NULL allowed)
+ * Synchronous.  Device memory: about 2 x 16 B x segment_edges of input buffers plus one
+ * segment graph and its batch scratch.  Errors as tm_graph_load and tm_run_batch. */
+typedef struct tm_stream_stats {
+    int64_t segments;          /* segment graphs built */
+    int64_t edges_copied;      /* edges copied to the device (overlaps counted again) */
+    int64_t max_segment_edges; /* largest segment */
+    double wall_ms;            /* the whole call */
+    double copy_wait_ms;       /* time spent waiting for a segment's copy after matching */
+} tm_stream_stats;
+int tm_stream_run(const int32_t* src, const int32_t* dst, const int64_t* t, int64_t m, int32_t n_nodes,
+                  const tm_query* queries, int32_t n_queries, int64_t segment_edges, tm_result* results,
+                  tm_stream_stats* stats);
+
 /* ---- prepared batches (CUDA graph) ----------------------------------------------
  * A fixed set of queries on one graph, prepared once and launched many times:
  * plans and weight tables are built at creation, scratch is sized for the worst

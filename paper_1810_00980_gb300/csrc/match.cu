@@ -410,10 +410,10 @@ __global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int 
             W.thi[w] = G.m;
         } else {
             k = (int32_t)(r / Q.J);
-            j = r % Q.J + 1;
+            j = Q.j_lo + r % Q.J + 1;
             uint64_t h0 = draw(Q.seed, (uint64_t)k, 0);
             int64_t s = -(int64_t)(h0 % (uint64_t)Q.cd);
-            start = s + (j - 1) * Q.cd;
+            start = s + (j - 1) * Q.cd - Q.t_off;
             tend = start + Q.cd - 1;
             lo = lower_bound_i64(G.t, 0, G.m, start);
             hi = upper_bound_i64(G.t, lo, G.m, tend);
@@ -428,7 +428,7 @@ __global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int 
                 hi = base + b;
             }
             if (Q.q_mode == TM_Q_EDGES) {
-                qj = G.m > 0 ? Q.p * (double)(hi - lo) / (double)G.m : 0.0;
+                qj = Q.m_total > 0 ? Q.p * (double)(hi - lo) / (double)Q.m_total : 0.0;
                 if (qj > 1.0) qj = 1.0;
             } else {
                 qj = Q.p;
@@ -558,8 +558,10 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
         first_edge(G, Q.order, e1, s1, d1, t1);
         int64_t thi = min(t1 + Q.delta, A.W.tend[wi]);
         int64_t len = 0, lo = 0, ha = 0, hh = 0;
-        acc.f[A_FIRST] += 1;
-        if (s1 != d1) {
+        // a segment of a streamed graph owns the exact queries' first edges in [own_lo, own_hi)
+        bool owned = t1 >= Q.own_lo && t1 < Q.own_hi;
+        if (owned) acc.f[A_FIRST] += 1;
+        if (owned && s1 != d1) {
             if (Q.l == 1) {
                 acc.f[A_COUNT] += 1;
                 if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, 0);
@@ -1007,7 +1009,8 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
 }
 
 // per query: sums over its windows, per shift; Z_k and the mean (Algorithm 1)
-__global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __restrict__ res) {
+__global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __restrict__ res,
+                       ShiftSums* __restrict__ sums) {
     int qi = blockIdx.x;
     const QPlan& Q = plans[qi];
     __shared__ double sh_d[2][32];
@@ -1071,6 +1074,11 @@ __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __r
                 L = x;
                 z2 += sh_d[0][ww];
                 v2 += sh_d[1][ww];
+            }
+            if (sums) {
+                ShiftSums& o = sums[Q.sum_base + k];
+                o.count = u[A_COUNT]; o.wlo = L; o.whi = H; o.first = u[A_FIRST]; o.cand = u[A_CAND];
+                o.last = u[A_LAST]; o.inst = u[A_INST]; o.kept = u[A_N]; o.zq = z2; o.vq = v2;
             }
             if (H >= (1ull << 63) || u[A_COUNT] >= (1ull << 63)) overflow = 1;
             for (int i = 0; i <= A_N; i++)
@@ -1156,7 +1164,7 @@ __global__ void k_plain(GraphDevT<TT> G, const QPlan* __restrict__ plan, unsigne
 // --------------------------------------------------------------- host side
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int validate_query(const tm_graph* g, const tm_query& q, std::string& why) {
+int validate_query_t(int64_t t_max, const tm_query& q, std::string& why) {
     if (!q.motif) { why = "motif is NULL"; return TM_EINVAL; }
     if (q.delta < 0) { why = "delta < 0"; return TM_EINVAL; }
     if (q.delta >= ((int64_t)1 << 61)) { why = "delta >= 2^61"; return TM_EINVAL; }
@@ -1170,14 +1178,21 @@ int validate_query(const tm_graph* g, const tm_query& q, std::string& why) {
         if (q.q_mode == TM_Q_EDGES && !(q.p > 0.0 && std::isfinite(q.p))) { why = "r must be > 0"; return TM_EINVAL; }
         __int128 cd = (__int128)q.c * q.delta;
         if (cd >= ((__int128)1 << 61)) { why = "c*delta >= 2^61"; return TM_EINVAL; }
-        int64_t J = 1 + (g->t_max + (int64_t)cd - 1) / (int64_t)cd;
+        int64_t J = 1 + (t_max + (int64_t)cd - 1) / (int64_t)cd;
         if ((__int128)J * q.b > ((__int128)1 << 31)) { why = "too many windows (b * J > 2^31)"; return TM_EINVAL; }
     }
     return TM_OK;
 }
 
+int validate_query(const tm_graph* g, const tm_query& q, std::string& why) {
+    return validate_query_t(g->t_max, q, why);
+}
+
 void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
     std::memset(&P, 0, sizeof(P));
+    P.own_lo = INT64_MIN;
+    P.own_hi = INT64_MAX;
+    P.m_total = g->m;
     const tm_motif* m = q.motif;
     P.l = m->l;
     P.k = m->k;
@@ -1263,6 +1278,8 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
 
 // the two-node tables the batch's two-node queries read: own when the middle and the last
 // edge are on the same pair, rev otherwise
+int check_query(int64_t t_max, const tm_query& q, std::string& why) { return validate_query_t(t_max, q, why); }
+
 template <typename TT>
 int ex_tables_for(const tm_graph* g, const std::vector<QPlan>& hp, cudaStream_t st, GraphDevT<TT>& G) {
     bool need_own = false, need_rev = false;
@@ -1285,7 +1302,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     std::vector<QPlan> hp((size_t)nq);
     std::vector<int> qstat((size_t)nq, TM_OK);
     int first_err = TM_OK;
-    int64_t NW = 0;
+    int64_t NW = 0, n_sums = 0;
     int lmax = 1, kmax = 2;
     bool any_hoist = false, any_full = false;
     size_t wtab_bytes = 0, full_bytes = 0;
@@ -1302,7 +1319,25 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             continue;
         }
         fill_plan(hp[(size_t)i], qs[i], g);
+        if (dbg && dbg->seg) {
+            // a segment of a streamed graph: the windows and first edges it owns
+            QPlan& P = hp[(size_t)i];
+            const SegSpec& S = dbg->seg[i];
+            P.t_off = S.t_off;
+            P.m_total = S.m_total;
+            P.full = 0;
+            if (P.mode == TM_MODE_ESTIMATE) {
+                P.order = kOrdTime;
+                P.j_lo = S.j_lo;
+                P.J = S.J;
+            } else {
+                P.own_lo = S.own_lo;
+                P.own_hi = S.own_hi;
+            }
+        }
         hp[(size_t)i].win_base = NW;
+        hp[(size_t)i].sum_base = n_sums;
+        n_sums += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].b;
         NW += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].J * hp[(size_t)i].b;
         lmax = std::max(lmax, hp[(size_t)i].l);
         kmax = std::max(kmax, hp[(size_t)i].k);
@@ -1320,7 +1355,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     size_t Ms = (size_t)std::max<int64_t>(g->m, 1);
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
-                full_bytes + (any_full ? 3 * a256(4 * Ms) : 0);
+                full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
+                a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
     char* p = sb;
@@ -1358,6 +1394,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     int64_t* dF = (int64_t*)take(8);
     int64_t* dW2 = (int64_t*)take(8);
     unsigned long long* dctr = (unsigned long long*)take(8);
+    ShiftSums* dsums = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
 
     int rc = TM_OK;
     auto fail = [&](cudaError_t e, const char* what) {
@@ -1475,12 +1512,17 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     if (rc == TM_OK) {
         int ev_f0 = pe.mark(st);
-        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres); count_launch();
+        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, dbg && dbg->sums ? dsums : nullptr); count_launch();
         fail(cudaGetLastError(), "k_fold");
         ev_f1 = pe.mark(st);
         if (ev_m1 < 0) ev_m1 = ev_f0;
     }
     if (rc == TM_OK) fail(cudaMemcpyAsync(res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
+    if (rc == TM_OK && dbg && dbg->sums && n_sums > 0) {
+        std::memset(dbg->sums, 0, sizeof(ShiftSums) * (size_t)n_sums);   // rejected queries write none
+        fail(cudaMemcpyAsync(dbg->sums, dsums, sizeof(ShiftSums) * (size_t)n_sums, cudaMemcpyDeviceToHost, st),
+             "shift sums");
+    }
     // optional window readback for one query
     std::vector<int64_t> h_lo, h_hi, h_start, h_j;
     std::vector<int32_t> h_k, h_kept;
@@ -1743,7 +1785,7 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
     }
-    k_fold<<<1, 256, 0, st>>>(dplan, W, dres); count_launch();
+    k_fold<<<1, 256, 0, st>>>(dplan, W, dres, nullptr); count_launch();
     e = cudaGetLastError();
     tm_result hres;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st);
@@ -1964,7 +2006,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         }
     }
     if (rc == TM_OK) {
-        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres); count_launch();
+        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, nullptr); count_launch();
         fail(cudaGetLastError(), "k_fold");
     }
     fail(cudaMemcpyAsync(b->h_res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");

@@ -187,6 +187,13 @@ struct QPlan {
     double p;
     uint64_t seed;
     const uint64_t* wtab;// [2*(delta+1)] Q64 weights c delta / (c delta - Delta), or null
+    // a segment of a streamed graph (defaults: the whole graph)
+    int64_t t_off;       // window time origin minus the graph's time origin
+    int64_t j_lo;        // windows j_lo+1 .. j_lo+J of every shift are processed
+    int64_t own_lo;      // exact queries: first edges with time in [own_lo, own_hi)
+    int64_t own_hi;
+    int64_t m_total;     // |T| in q_j = r |T_j| / |T|
+    int64_t sum_base;    // first per-shift sums slot of this query
     LevelPlan lv[TM_L_MAX];
 };
 
@@ -198,6 +205,20 @@ struct Tuning {
 };
 Tuning& tuning();
 
+// one query's part of a segment of a streamed graph
+struct SegSpec {
+    int64_t t_off;           // global time of the segment graph's time 0
+    int64_t j_lo, J;         // estimate: windows j_lo+1 .. j_lo+J of every shift
+    int64_t own_lo, own_hi;  // exact: first edges with (segment) time in [own_lo, own_hi)
+    int64_t m_total;         // edges of the whole graph
+};
+
+// one shift's sums over the windows a batch processed (additive across segments)
+struct ShiftSums {
+    unsigned long long count, wlo, whi, first, cand, last, inst, kept;
+    double zq, vq;
+};
+
 struct BatchOut {                 // optional per-window readback for one query
     int query = -1;
     int32_t k = 0;
@@ -206,11 +227,15 @@ struct BatchOut {                 // optional per-window readback for one query
     int64_t cap = 0;
     int64_t n_out = 0;
     int64_t shift = 0;
+    const SegSpec* seg = nullptr; // per query, or null (whole graph)
+    ShiftSums* sums = nullptr;    // host: per query, per shift (exact: one), or null
 };
 
 int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res,
               cudaStream_t st, BatchOut* dbg);
 int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* count);
+// query checks of tm_run_batch against a graph whose normalised times end at t_max
+int check_query(int64_t t_max, const tm_query& q, std::string& why);
 
 // primitives (prims.cu)
 int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,

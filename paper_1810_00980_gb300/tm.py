@@ -93,6 +93,7 @@ _SIGS = {
     "tm_estimate_windows": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i32, _c_dbl, _c_u64, _c_i32, _c_i32,
                                            _vp, _c_i64, _vp, _vp]),
     "tm_run_batch": (ctypes.c_int, [_vp, _vp, _c_i32, _vp, _vp]),
+    "tm_stream_run": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i32, _vp, _c_i32, _c_i64, _vp, _vp]),
     "tm_batch_create": (ctypes.c_int, [_vp, _vp, _c_i32, _vp]),
     "tm_batch_launch": (ctypes.c_int, [_vp, _vp]),
     "tm_batch_results": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -332,6 +333,32 @@ class Batch:
 
     def results(self):
         return [_result_dict(self.rarr[i]) for i in range(self.n)]
+
+
+class StreamStatsC(ctypes.Structure):
+    _fields_ = [("segments", _c_i64), ("edges_copied", _c_i64), ("max_segment_edges", _c_i64),
+                ("wall_ms", _c_dbl), ("copy_wait_ms", _c_dbl)]
+
+
+def stream_run(src, dst, t, queries, segment_edges: int, n_nodes: int, check: bool = True):
+    """tm_stream_run: the queries over a time-sorted edge list in host memory (numpy
+    arrays or CPU tensors, pinned tensors copied directly), in chronological segments
+    of about `segment_edges` edges.  Returns (results, stats)."""
+    if hasattr(src, "data_ptr") and hasattr(src, "is_pinned") and src.is_pinned():
+        keep = (src, dst, t)
+    else:
+        keep = (_host(src, np.int32), _host(dst, np.int32), _host(t, np.int64))
+    a, b, c = keep
+    m = int(c.numel()) if hasattr(c, "numel") else len(c)
+    qs = list(queries)
+    qarr = (QueryC * max(len(qs), 1))(*[q.to_c() for q in qs])
+    rarr = (ResultC * max(len(qs), 1))()
+    st = StreamStatsC()
+    s = lib().tm_stream_run(_ptr(a), _ptr(b), _ptr(c), m, int(n_nodes), ctypes.cast(qarr, _vp), len(qs),
+                            int(segment_edges), ctypes.cast(rarr, _vp), ctypes.byref(st))
+    if check:
+        _check(s, "tm_stream_run")
+    return [_result_dict(rarr[i]) for i in range(len(qs))], {f: getattr(st, f) for f, _ in StreamStatsC._fields_}
 
 
 class PreparedBatch:

@@ -50,11 +50,12 @@ def test_nm_shows_exports(built):
 def test_struct_layouts_match_c(built, tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tm.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                     'sizeof(tm_graph_info), sizeof(tm_window_rec), sizeof(tm_query), sizeof(tm_result),'
                     'sizeof(tm_tuning), sizeof(tm_serve_cfg), offsetof(tm_result, var_hat),'
                     'offsetof(tm_profile, launches),'
-                    'offsetof(tm_query, q_mode));return 0;}\n')
+                    'offsetof(tm_query, q_mode), sizeof(tm_stream_stats),'
+                    'offsetof(tm_stream_stats, copy_wait_ms));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = [int(x) for x in subprocess.check_output([str(exe)]).split()]
@@ -62,7 +63,26 @@ def test_struct_layouts_match_c(built, tmp_path):
     tm = built
     assert vals == [ctypes.sizeof(tm.GraphInfo), ctypes.sizeof(tm.WindowRec), ctypes.sizeof(tm.QueryC),
                     ctypes.sizeof(tm.ResultC), ctypes.sizeof(tm.TuningC), ctypes.sizeof(tm.ServeCfg),
-                    tm.ResultC.var_hat.offset, tm.ProfileC.launches.offset, tm.QueryC.q_mode.offset]
+                    tm.ResultC.var_hat.offset, tm.ProfileC.launches.offset, tm.QueryC.q_mode.offset,
+                    ctypes.sizeof(tm.StreamStatsC), tm.StreamStatsC.copy_wait_ms.offset]
+
+
+def test_stream_run_validates_on_the_host(built):
+    """tm_stream_run's argument checks run before any device call."""
+    import numpy as np
+    tm = built
+    mo = tm.Motif([0, 1, 2], [1, 2, 0])
+    s = np.array([0, 1, 2], np.int32)
+    d = np.array([1, 2, 0], np.int32)
+    with pytest.raises(tm.TmError) as e:
+        tm.stream_run(s, d, np.array([5, 3, 9], np.int64), [tm.exact_query(mo, 10)], 2, 3)
+    assert e.value.status == tm.TM_EUNSORTED
+    for seg, n in ((0, 3), (2, 0)):
+        with pytest.raises(tm.TmError) as e:
+            tm.stream_run(s, d, np.array([1, 2, 3], np.int64), [tm.exact_query(mo, 10)], seg, n)
+        assert e.value.status == tm.TM_EINVAL
+    res, st = tm.stream_run(s, d, np.array([1, 2, 3], np.int64), [], 2, 3)
+    assert res == [] and st["segments"] == 0
 
 
 def test_strerror_without_gpu(built):
