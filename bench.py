@@ -517,6 +517,7 @@ def main():
     ap.add_argument("--serve-full", action="store_true",
                     help="serving run on four resident graphs of 1M, 10M, 25M and 50M edges")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-stream", action="store_true", help="skip the host-streaming measurement")
     ap.add_argument("--workload", default="config2", choices=["config2", "config3", "config5"])
     ap.add_argument("--tuning", default="auto",
                     help="'auto' (autotune on the batch) or block_threads,blocks_per_sm,chunk_items,enum_threshold")
@@ -661,6 +662,26 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
 
+    # streaming: the same batch over the edge list in pinned host memory, in chronological
+    # segments (outside the timed step); results must equal the resident batch's
+    stream = None
+    if not args.no_stream:
+        n_nodes = int(max(int(src.max()), int(dst.max()))) + 1
+        stream = {"segments": []}
+        for seg in (M // 8, M // 2):
+            tm.stream_run(h_src, h_dst, h_t, qs, seg, n_nodes)
+            walls, st = [], None
+            for _ in range(3):
+                res_s, st = tm.stream_run(h_src, h_dst, h_t, qs, seg, n_nodes)
+                walls.append(st["wall_ms"])
+            wall = statistics.median(walls)
+            same = all(a["count"] == b["count"] and a["estimate"] == b["estimate"]
+                       for a, b in zip(res_s, batch.results()))
+            stream["segments"].append({"segment_edges": seg, "segments": st["segments"],
+                                       "edges_copied": st["edges_copied"], "wall_ms": wall,
+                                       "queries_per_s": nq / (wall / 1e3), "edges_per_s": M / (wall / 1e3),
+                                       "copy_wait_ms": st["copy_wait_ms"], "results_equal_resident": same})
+
     # serving: continuous batching on resident graphs (outside the timed step)
     serve = None
     if not args.no_serve:
@@ -746,6 +767,7 @@ def main():
         "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 16 * M,
                 "d2h_bytes_per_step": nq * ctypes.sizeof(tm.ResultC)},
         "serve": serve,
+        "stream": stream,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
