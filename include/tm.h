@@ -56,6 +56,18 @@ extern "C" {
 
 #define TM_Q_UNIFORM 0   /* q_j = p for every window */
 #define TM_Q_EDGES 1     /* q_j = min(1, r |T_j| / |T|) with r = the query's p field (Eq. 9) */
+/* TM_Q_AUTO: uniform q_j = p with p chosen for a target relative error (the query's p field,
+ * in (0, 1)) at 95 % confidence (z = 1.96).  A pilot estimate with p0 = TM_AUTO_PILOT_P and
+ * the same c and b (seed ^ TM_AUTO_PILOT_SEED_XOR) gives Z0 and var_hat0; since var_hat is
+ * unbiased for Var[Z | s] = sum_j Y_j^2 (1 - p)/p (Lemma 4.4), S2 = var_hat0 p0 / (1 - p0)
+ * estimates sum_j Y_j^2, and the smallest p with z sqrt(S2 (1 - p) / (p b)) <= target Z0 is
+ *   p = 1 / (1 + b (target Z0 / z)^2 / S2), clamped to [p0, 1] (p = 1 when Z0 = 0).
+ * The shift variance (Lemma 4.2) is not part of this target.  The query then runs with that
+ * p and its own seed; results.p_used reports it.  tm_run_batch and the server only (a
+ * prepared batch or a stream rejects it with TM_EINVAL). */
+#define TM_Q_AUTO 2
+#define TM_AUTO_PILOT_P 0.05
+#define TM_AUTO_PILOT_SEED_XOR 0xA5A5A5A5A5A5A5A5ull
 
 typedef struct tm_graph tm_graph;
 typedef struct tm_motif tm_motif;
@@ -89,10 +101,11 @@ typedef struct {
     int64_t delta;        /* time span delta (Def. 2.2) */
     int32_t mode;         /* TM_MODE_EXACT or TM_MODE_ESTIMATE */
     int32_t c;            /* window width factor: windows are c*delta ticks wide (Eq. 1) */
-    double p;             /* TM_Q_UNIFORM: keep probability; TM_Q_EDGES: the constant r */
+    double p;             /* TM_Q_UNIFORM: keep probability; TM_Q_EDGES: the constant r;
+                             TM_Q_AUTO: the target relative error */
     uint64_t seed;        /* random draws of Algorithm 1 (SplitMix64, see tm_estimate) */
     int32_t b;            /* number of shifts averaged (Algorithm 1 outer loop), >= 1 */
-    int32_t q_mode;       /* TM_Q_UNIFORM or TM_Q_EDGES */
+    int32_t q_mode;       /* TM_Q_UNIFORM, TM_Q_EDGES or TM_Q_AUTO */
 } tm_query;
 
 typedef struct {
@@ -108,6 +121,10 @@ typedef struct {
     int64_t inst_read;    /* last-edge entries read one by one (estimate mode) */
     double var_hat;       /* estimate: unbiased estimate of Var[Z | s] averaged over shifts
                              (Lemma 4.4: sum_j Q_j Y_j^2 (1-q_j)/q_j^2); exact: 0 */
+    double shift_var;     /* estimate with b >= 2: sample variance of the b per-shift Z_k (an
+                             unbiased estimate of Var[Z_k], shift variance included), so
+                             estimate +- 1.96 sqrt(shift_var / b) is a 95 % interval; else 0 */
+    double p_used;        /* estimate: the p (or r) the windows were kept with; exact: 1 */
 } tm_result;
 
 /* ---- errors -------------------------------------------------------------- */

@@ -1019,7 +1019,7 @@ __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __r
     int64_t nwin = Q.mode == TM_MODE_EXACT ? 1 : Q.J;
     int nsh = Q.mode == TM_MODE_EXACT ? 1 : Q.b;
     if (Q.l <= 0) nsh = 0;   // query rejected on the host
-    double zsum = 0.0, vsum = 0.0;
+    double zsum = 0.0, vsum = 0.0, wmean = 0.0, wm2 = 0.0;   // Welford over the per-shift Z_k
     unsigned long long tot[A_N + 1] = {0};   // + kept windows
     int overflow = 0;
     for (int k = 0; k < nsh; k++) {
@@ -1087,6 +1087,9 @@ __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __r
             double zk = Q.q_mode == TM_Q_EDGES ? z2 : Wd / Q.p;
             zsum += zk;
             vsum += v2;
+            double dz = zk - wmean;
+            wmean += dz / (k + 1);
+            wm2 += dz * (zk - wmean);
         }
         __syncthreads();
     }
@@ -1100,11 +1103,14 @@ __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __r
             r.windows = 1;
             r.windows_kept = 1;
             r.var_hat = 0.0;
+            r.p_used = 1.0;
         } else {
             r.estimate = nsh ? zsum / nsh : 0.0;
             r.windows = (int64_t)nsh * Q.J;
             r.windows_kept = (int64_t)tot[A_N];
             r.var_hat = nsh ? vsum / nsh : 0.0;
+            r.shift_var = nsh >= 2 ? wm2 / (nsh - 1) : 0.0;
+            r.p_used = Q.p;
         }
         r.first_edges = (int64_t)tot[A_FIRST];
         r.cand_edges = (int64_t)tot[A_CAND];
@@ -1173,7 +1179,11 @@ int validate_query_t(int64_t t_max, const tm_query& q, std::string& why) {
         if (q.delta < 1) { why = "estimate needs delta >= 1"; return TM_EINVAL; }
         if (q.c < 1) { why = "c < 1"; return TM_EINVAL; }
         if (q.b < 1 || q.b > (1 << 20)) { why = "b outside [1, 2^20]"; return TM_EINVAL; }
-        if (q.q_mode != TM_Q_UNIFORM && q.q_mode != TM_Q_EDGES) { why = "bad q_mode"; return TM_EINVAL; }
+        if (q.q_mode != TM_Q_UNIFORM && q.q_mode != TM_Q_EDGES && q.q_mode != TM_Q_AUTO) {
+            why = "bad q_mode";
+            return TM_EINVAL;
+        }
+        if (q.q_mode == TM_Q_AUTO && !(q.p > 0.0 && q.p < 1.0)) { why = "target error outside (0, 1)"; return TM_EINVAL; }
         if (q.q_mode == TM_Q_UNIFORM && !(q.p > 0.0 && q.p <= 1.0)) { why = "p outside (0, 1]"; return TM_EINVAL; }
         if (q.q_mode == TM_Q_EDGES && !(q.p > 0.0 && std::isfinite(q.p))) { why = "r must be > 0"; return TM_EINVAL; }
         __int128 cd = (__int128)q.c * q.delta;
@@ -1593,10 +1603,64 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     return first_err;
 }
 
-int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
-              BatchOut* dbg) {
+namespace {
+
+int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
+                   BatchOut* dbg) {
     if (g && g->dev.tbytes == 4) return run_batch_t<int32_t>(g, qs, nq, res, st, dbg);
     return run_batch_t<int64_t>(g, qs, nq, res, st, dbg);
+}
+
+// TM_Q_AUTO: p from a pilot estimate (see tm.h): the smallest p whose sampling standard
+// deviation of the b-shift mean, predicted from the pilot's Var[Z | s] estimate (Lemma 4.4),
+// is within target * Z0 / z
+double auto_p(const tm_result& pilot, double target, int32_t b) {
+    const double z = 1.96, p0 = TM_AUTO_PILOT_P;
+    double z0 = pilot.estimate;
+    double s2 = pilot.var_hat * p0 / (1.0 - p0);   // estimates sum_j Y_j^2
+    if (!(z0 > 0.0)) return 1.0;
+    if (!(s2 > 0.0)) return p0;
+    double r = (double)b * (target * z0 / z) * (target * z0 / z) / s2;
+    double p = 1.0 / (1.0 + r);
+    return std::min(1.0, std::max(p0, p));
+}
+
+}  // namespace
+
+int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
+              BatchOut* dbg) {
+    bool any_auto = false;
+    for (int i = 0; qs && i < nq; i++)
+        any_auto |= qs[i].mode == TM_MODE_ESTIMATE && qs[i].q_mode == TM_Q_AUTO;
+    if (!any_auto) return run_batch_once(g, qs, nq, res, st, dbg);
+    if (!g || !res) { set_error("NULL argument"); return TM_EINVAL; }
+    if (dbg && (dbg->seg || dbg->query >= 0)) { set_error("TM_Q_AUTO needs the whole graph"); return TM_EINVAL; }
+    // pilot batch: the auto queries at p0 (valid ones only; the rest is checked below)
+    std::vector<tm_query> pq;
+    std::vector<int> pidx;
+    for (int i = 0; i < nq; i++) {
+        if (qs[i].mode != TM_MODE_ESTIMATE || qs[i].q_mode != TM_Q_AUTO) continue;
+        std::string why;
+        if (validate_query(g, qs[i], why) != TM_OK) continue;
+        tm_query q = qs[i];
+        q.q_mode = TM_Q_UNIFORM;
+        q.p = TM_AUTO_PILOT_P;
+        q.seed = qs[i].seed ^ TM_AUTO_PILOT_SEED_XOR;
+        pq.push_back(q);
+        pidx.push_back(i);
+    }
+    std::vector<tm_result> pr(pq.size());
+    std::vector<tm_query> fq(qs, qs + nq);
+    if (!pq.empty()) {
+        int rc = run_batch_once(g, pq.data(), (int)pq.size(), pr.data(), st, nullptr);
+        if (rc != TM_OK) return rc;
+        for (size_t x = 0; x < pq.size(); x++) {
+            tm_query& q = fq[(size_t)pidx[x]];
+            q.p = auto_p(pr[x], qs[pidx[x]].p, q.b);
+            q.q_mode = TM_Q_UNIFORM;
+        }
+    }
+    return run_batch_once(g, fq.data(), nq, res, st, dbg);
 }
 
 template <typename TT>
@@ -1614,6 +1678,7 @@ int count_plain_t(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* 
     TM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     char* sb = nullptr;
     int rc = TM_OK;
+    static_assert(sizeof(QPlan) <= 256, "the plan and the counter share a 512-byte block");
     cudaError_t e = cudaMallocAsync((void**)&sb, 512, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sb, &P, sizeof(P), cudaMemcpyHostToDevice, st);
     unsigned long long* dc = (unsigned long long*)(sb + 256);
@@ -1863,6 +1928,10 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     for (int i = 0; i < nq; i++) {
         std::string why;
         int s = validate_query(g, qs[i], why);
+        if (s == TM_OK && qs[i].mode == TM_MODE_ESTIMATE && qs[i].q_mode == TM_Q_AUTO) {
+            s = TM_EINVAL;   // p is chosen on the host from a pilot run: not a fixed sequence
+            why = "TM_Q_AUTO needs tm_run_batch";
+        }
         QPlan& P = hp[(size_t)i];
         if (s != TM_OK) {
             b->qstat[(size_t)i] = s;

@@ -187,6 +187,10 @@ extern "C" int tm_stream_run(const int32_t* src, const int32_t* dst, const int64
         std::memset(&results[i], 0, sizeof(tm_result));
         std::string why;
         int s = check_query(tmax, q, why);
+        if (s == TM_OK && q.mode == TM_MODE_ESTIMATE && q.q_mode == TM_Q_AUTO) {
+            s = TM_EINVAL;   // the pilot would need the whole graph
+            why = "TM_Q_AUTO needs tm_run_batch";
+        }
         if (s != TM_OK) {
             results[i].status = s;
             if (first_err == TM_OK) { first_err = s; set_error("query " + std::to_string(i) + ": " + why); }
@@ -353,15 +357,19 @@ extern "C" int tm_stream_run(const int32_t* src, const int32_t* dst, const int64
             const tm_query& q = queries[i];
             tm_result& r = results[i];
             unsigned long long cnt = 0, first = 0, cand = 0, last = 0, inst = 0, kept = 0;
-            double zsum = 0.0, vsum = 0.0;
+            double zsum = 0.0, vsum = 0.0, wmean = 0.0, wm2 = 0.0;
             bool overflow = false;
             for (int k = 0; k < Q.b; k++) {
                 const ShiftSums& S = Q.acc[(size_t)k];
                 cnt += S.count; first += S.first; cand += S.cand; last += S.last; inst += S.inst; kept += S.kept;
                 if (S.whi >= (1ull << 63) || S.count >= (1ull << 63)) overflow = true;
                 double Wd = (double)S.whi + (double)S.wlo * 0x1.0p-64;
-                zsum += q.q_mode == TM_Q_EDGES ? S.zq : Wd / q.p;
+                double zk = q.q_mode == TM_Q_EDGES ? S.zq : Wd / q.p;
+                zsum += zk;
                 vsum += S.vq;
+                double dz = zk - wmean;
+                wmean += dz / (k + 1);
+                wm2 += dz * (zk - wmean);
             }
             r.status = overflow ? TM_EOVERFLOW : TM_OK;
             r.count = (int64_t)cnt;
@@ -369,11 +377,14 @@ extern "C" int tm_stream_run(const int32_t* src, const int32_t* dst, const int64
                 r.estimate = (double)cnt;
                 r.windows = 1;
                 r.windows_kept = 1;
+                r.p_used = 1.0;
             } else {
                 r.estimate = zsum / Q.b;
                 r.windows = (int64_t)Q.b * Q.J;
                 r.windows_kept = (int64_t)kept;
                 r.var_hat = vsum / Q.b;
+                r.shift_var = Q.b >= 2 ? wm2 / (Q.b - 1) : 0.0;
+                r.p_used = q.p;
             }
             r.first_edges = (int64_t)first;
             r.cand_edges = (int64_t)cand;

@@ -21,7 +21,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libtmotif.so")
 TM_OK, TM_EINVAL, TM_EUNSORTED, TM_ERANGE, TM_ENOMEM, TM_EADMIT, TM_ETIMEOUT = range(7)
 TM_ESTACK, TM_EOVERFLOW, TM_ECUDA, TM_PENDING, TM_ENOTFOUND, TM_ECANCELLED, TM_ESHUTDOWN = range(7, 14)
 TM_MODE_EXACT, TM_MODE_ESTIMATE = 0, 1
-TM_Q_UNIFORM, TM_Q_EDGES = 0, 1
+TM_Q_UNIFORM, TM_Q_EDGES, TM_Q_AUTO = 0, 1, 2
+TM_AUTO_PILOT_P = 0.05
+TM_AUTO_PILOT_SEED_XOR = 0xA5A5A5A5A5A5A5A5
 L_MAX = 8
 K_MAX = 8
 
@@ -47,7 +49,7 @@ class ResultC(ctypes.Structure):
     _fields_ = [("status", _c_i32), ("pad0", _c_i32), ("count", _c_i64), ("estimate", _c_dbl),
                 ("windows", _c_i64), ("windows_kept", _c_i64), ("first_edges", _c_i64),
                 ("cand_edges", _c_i64), ("last_ranges", _c_i64), ("inst_read", _c_i64),
-                ("var_hat", _c_dbl)]
+                ("var_hat", _c_dbl), ("shift_var", _c_dbl), ("p_used", _c_dbl)]
 
 
 class TuningC(ctypes.Structure):

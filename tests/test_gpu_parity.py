@@ -538,3 +538,68 @@ def test_two_node_motifs_mid_graph_exact_estimate(tm, orc):
         assert a["count"] == b_["count"] == c_["count"]
         assert a["estimate"] == b_["estimate"] == c_["estimate"]
     pb.free()
+
+
+def _auto_p(pilot, target, b):
+    """The pilot rule stated for TM_Q_AUTO, in the same floating-point steps."""
+    z, p0 = 1.96, 0.05
+    z0 = pilot["estimate"]
+    s2 = pilot["var_hat"] * p0 / (1.0 - p0)
+    if not z0 > 0.0:
+        return 1.0
+    if not s2 > 0.0:
+        return p0
+    r = float(b) * (target * z0 / z) * (target * z0 / z) / s2
+    return min(1.0, max(p0, 1.0 / (1.0 + r)))
+
+
+def test_auto_p_from_pilot_variance(tm, orc):
+    """TM_Q_AUTO: p chosen from a pilot's Lemma 4.4 variance estimate; the result is
+    the plain uniform estimate at that p (checked against the oracle), and
+    shift_var is the sample variance of the per-shift estimates."""
+    src, dst, t = synth.chung_lu_hawkes(3000, 300_000, 2.1, seed=61, horizon=6_000_000)
+    g = _graph(tm, src, dst, t)
+    for name in ("cycle3", "outstar3", "pingpong"):
+        ms, md = synth.MOTIFS[name]
+        mo = tm.Motif(ms, md)
+        exact = tm.count_exact(g, mo, 3600)
+        for seed in (3, 4):
+            q = tm.estimate_query(mo, 3600, 10, 0.05, seed, b=2, q_mode=tm.TM_Q_AUTO)
+            r = tm.run_batch(g, [q])[0]
+            pilot = tm.run_batch(g, [tm.estimate_query(mo, 3600, 10, tm.TM_AUTO_PILOT_P,
+                                                       seed ^ tm.TM_AUTO_PILOT_SEED_XOR, b=2)])[0]
+            p = _auto_p(pilot, 0.05, 2)
+            assert r["p_used"] == p and 0.05 <= p <= 1.0
+            plain = tm.run_batch(g, [tm.estimate_query(mo, 3600, 10, p, seed, b=2)])[0]
+            assert r["estimate"] == plain["estimate"] and r["shift_var"] == plain["shift_var"]
+            zo = orc.estimate(src, dst, t, ms, md, 3600, 10, p, seed, b=2, threads=8)
+            assert _close(r["estimate"], zo)
+            # shift_var: sample variance of the two per-shift estimates
+            zk = []
+            for k in range(2):
+                _, recs = tm.estimate_windows(g, mo, 3600, 10, p, seed, k=k)
+                zk.append(sum(x["w_int"] + x["w_frac"] * 2.0 ** -64 for x in recs) / p)
+            sv = (zk[0] - zk[1]) ** 2 / 2.0
+            assert abs(r["shift_var"] - sv) <= 1e-9 * max(sv, 1.0)
+        assert exact > 0
+    # not available where p cannot be chosen at run time
+    q = tm.estimate_query(mo, 3600, 10, 0.05, 1, q_mode=tm.TM_Q_AUTO)
+    pb = tm.PreparedBatch(g, [q])
+    pb.launch()
+    assert pb.results(check=False)[0]["status"] == tm.TM_EINVAL
+    pb.free()
+    res, _ = tm.stream_run(src, dst, t, [q], 100_000, int(max(src.max(), dst.max())) + 1, check=False)
+    assert res[0]["status"] == tm.TM_EINVAL
+
+
+def test_auto_p_meets_target_on_most_seeds(tm):
+    """With target 5 % the sampling error stays near the target (the shift variance
+    is not part of the rule, so the bound is loose: 80 % of seeds within 10 %)."""
+    src, dst, t = synth.chung_lu_hawkes(3000, 300_000, 2.1, seed=62, horizon=6_000_000)
+    g = _graph(tm, src, dst, t)
+    mo = tm.Motif(*synth.MOTIFS["cycle3"])
+    exact = tm.count_exact(g, mo, 3600)
+    qs = [tm.estimate_query(mo, 3600, 30, 0.05, 100 + s, b=2, q_mode=tm.TM_Q_AUTO) for s in range(20)]
+    res = tm.run_batch(g, qs)
+    errs = [abs(r["estimate"] - exact) / exact for r in res]
+    assert sum(e <= 0.10 for e in errs) >= 16, errs
