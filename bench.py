@@ -664,10 +664,10 @@ def main():
 
     # streaming: the same batch over the edge list in pinned host memory, in chronological
     # segments (outside the timed step); results must equal the resident batch's
-    stream = None
+    stream_res = None
     if not args.no_stream:
         n_nodes = int(max(int(src.max()), int(dst.max()))) + 1
-        stream = {"segments": []}
+        stream_res = {"segments": []}
         for seg in (M // 8, M // 2):
             tm.stream_run(h_src, h_dst, h_t, qs, seg, n_nodes)
             walls, st = [], None
@@ -677,10 +677,24 @@ def main():
             wall = statistics.median(walls)
             same = all(a["count"] == b["count"] and a["estimate"] == b["estimate"]
                        for a, b in zip(res_s, batch.results()))
-            stream["segments"].append({"segment_edges": seg, "segments": st["segments"],
+            stream_res["segments"].append({"segment_edges": seg, "segments": st["segments"],
                                        "edges_copied": st["edges_copied"], "wall_ms": wall,
                                        "queries_per_s": nq / (wall / 1e3), "edges_per_s": M / (wall / 1e3),
                                        "copy_wait_ms": st["copy_wait_ms"], "results_equal_resident": same})
+
+    # Fig. 4-style diagnostic: correlation of the window weights Y_j with the window edge
+    # counts |T_j| (what q_j = r |T_j| / |T| relies on), one shift with every window kept
+    q_corr = {}
+    g_dev = tm.Graph(d_src, d_dst, d_t)
+    for n in MOTIF_NAMES:
+        for d in (600, 3600):
+            c = EST_PARAMS[(n, d)][0]
+            _, recs = tm.estimate_windows(g_dev, motifs[n], d, c, 1.0, 7)
+            y = np.array([r["w_int"] + r["w_frac"] * 2.0 ** -64 for r in recs])
+            te = np.array([r["hi"] - r["lo"] for r in recs], dtype=np.float64)
+            ok = y.std() > 0 and te.std() > 0
+            q_corr[f"{n}@{d}"] = float(np.corrcoef(te, y)[0, 1]) if ok else None
+    g_dev.free()
 
     # serving: continuous batching on resident graphs (outside the timed step)
     serve = None
@@ -767,7 +781,8 @@ def main():
         "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 16 * M,
                 "d2h_bytes_per_step": nq * ctypes.sizeof(tm.ResultC)},
         "serve": serve,
-        "stream": stream,
+        "stream": stream_res,
+        "q_corr_edges_vs_weight": q_corr,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
