@@ -125,13 +125,16 @@ __global__ void k_pair_index(const uint32_t* __restrict__ perm, const int32_t* _
 // chain ends at an empty slot.
 __global__ void k_hash_insert(const int32_t* __restrict__ pair_src, const int32_t* __restrict__ pair_dst,
                               const int64_t* __restrict__ pair_off, int64_t P,
-                              unsigned long long* __restrict__ slots, unsigned long long mask) {
+                              unsigned long long* __restrict__ slots, unsigned long long mask,
+                              uint32_t* __restrict__ filt, unsigned long long fmask) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long key = ((unsigned long long)(uint32_t)pair_src[p] << 32) | (uint32_t)pair_dst[p];
         unsigned long long seg = ((unsigned long long)(uint32_t)(pair_off[p + 1] - pair_off[p]) << 32) |
                                  (uint32_t)pair_off[p];
-        unsigned long long h = sm64_mix(key) & mask;
+        unsigned long long h0 = sm64_mix(key);
+        atomicOr(filt + ((h0 >> 32) & fmask), (1u << (h0 & 31)) | (1u << ((h0 >> 5) & 31)));
+        unsigned long long h = h0 & mask;
         for (unsigned long long it = 0; it <= mask; it++) {
             unsigned long long prev = atomicCAS(&slots[2 * h], kHashEmpty, key);
             if (prev == kHashEmpty) {
@@ -272,6 +275,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     G.pk_off = pk_off; G.pair_dst = pair_dst; G.pair_off = pair_off; G.pair_t = pair_t;
     G.out_src = out_src; G.in_dst = in_dst; G.pair_pid = pair_pid;
     G.hslots = nullptr; G.hmask = 0;
+    G.pfilt = nullptr; G.pfmask = 0;
     g->hash_block = nullptr;
     g->ex_own_block = nullptr;
     g->ex_rev_block = nullptr;
@@ -376,20 +380,28 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_status(e, "graph build", __FILE__, __LINE__);
     }
-    // pair hash: capacity the next power of two >= 2 P
+    // pair hash: capacity the next power of two >= 2 P; then the pair filter: 8 bits per pair
+    // (a power of two of 32-bit words), at most 32 MB so that it stays in L2
     if (rc == TM_OK) {
         unsigned long long cap = 2;
         while (cap < 2ull * (unsigned long long)P) cap <<= 1;
-        e = cudaMallocAsync(&g->hash_block, 16 * cap, st);
+        unsigned long long fw = 1;
+        while (fw < ((unsigned long long)P + 3) / 4 && fw < (1ull << 23)) fw <<= 1;
+        e = cudaMallocAsync(&g->hash_block, 16 * cap + 4 * fw, st);
         if (e != cudaSuccess) rc = cuda_status(e, "cudaMalloc(pair hash)", __FILE__, __LINE__);
         if (rc == TM_OK) {
-            g->bytes += (int64_t)(16 * cap);
+            g->bytes += (int64_t)(16 * cap + 4 * fw);
             G.hslots = (const unsigned long long*)g->hash_block;
             G.hmask = cap - 1;
+            uint32_t* filt = (uint32_t*)((char*)g->hash_block + 16 * cap);
+            G.pfilt = filt;
+            G.pfmask = fw - 1;
             e = cudaMemsetAsync(g->hash_block, 0xff, 16 * cap, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(filt, 0, 4 * fw, st);
             if (e == cudaSuccess) {
                 k_hash_insert<<<grid_for(P), kThreads, 0, st>>>((const int32_t*)kt, pair_dst, pair_off, P,
-                                                               (unsigned long long*)g->hash_block, cap - 1);
+                                                               (unsigned long long*)g->hash_block, cap - 1,
+                                                               filt, fw - 1);
                 count_launch();
                 e = cudaGetLastError();
             }

@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                         pb = __ldg(G.pair_off + pid + 1);
                         own_ub = gallop_ub(G.pair_t, e1 + 1, pb, t1);
                     } else {
-                        pair_segment(G, s1, d1, pa, pb);   // e1 is one of the pair's edges
+                        pair_segment(G, s1, d1, pa, pb, false);   // e1 is one of the pair's edges
                         own_ub = upper_bound_i64(G.pair_t, pa, pb, t1);
                     }
                     have_own = true;
@@ -839,7 +839,8 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
 }
 
 // OCC: resident 256-thread blocks per SM the register allocation must allow
-// (three-edge motifs: 4 without spills, 6 with a few spilled registers)
+// (three-edge motifs: 4 without spills, 6 with spilled registers; four-edge motifs: 1 leaves
+// the compiler 118 registers, 4 caps them at 64 with spills -- the autotuner picks)
 template <typename TT, int LMAX, int KMAX, int OCC = (LMAX <= 3 ? 4 : 1)>
 __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
     const GraphDevT<TT>& G = A.G;
@@ -1510,6 +1511,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
                     k_match<TT, 3, 4, 6><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                else if (lmax <= 4 && kmax <= 4 && tu.blocks_per_sm >= 4)
+                    k_match<TT, 4, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
                 else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
@@ -2067,6 +2070,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
             if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
                 k_match<TT, 3, 4, 6><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+            else if (lmax <= 4 && kmax <= 4 && tu.blocks_per_sm >= 4)
+                k_match<TT, 4, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
             else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);

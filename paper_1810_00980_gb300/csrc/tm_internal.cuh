@@ -59,6 +59,10 @@ struct GraphDev {
     const int32_t* pair_pid;// [m] pair index of each pair-view entry
     const unsigned long long* hslots;  // [2*(hmask+1)]: key, then (length << 32 | begin) of the pair's segment
     unsigned long long hmask;          // hash capacity - 1 (power of two)
+    // pair filter: two bits per pair in one 32-bit word; a lookup whose two bits are not both
+    // set has no pair (most lookups of absent pairs end in this L2-resident array)
+    const uint32_t* pfilt;             // [pfmask+1] or null
+    unsigned long long pfmask;         // words - 1 (power of two)
     int32_t loops;          // 1 if some edge has src == dst
 };
 
@@ -86,6 +90,8 @@ struct GraphDevT {
     const int32_t* pair_pid;
     const unsigned long long* hslots;
     unsigned long long hmask;
+    const uint32_t* pfilt;
+    unsigned long long pfmask;
     int32_t loops;
     // two-node tables (set by the batch that needs them): over pair-view positions e,
     // exclusive prefix sums of the number of edges of e's own pair (ex_own) and of its
@@ -104,6 +110,7 @@ inline GraphDevT<TT> typed(const GraphDev& g) {
     r.pk_off = g.pk_off; r.pair_dst = g.pair_dst; r.pair_off = g.pair_off; r.pair_t = (const TT*)g.pair_t;
     r.out_src = g.out_src; r.in_dst = g.in_dst; r.pair_pid = g.pair_pid;
     r.hslots = g.hslots; r.hmask = g.hmask; r.loops = g.loops;
+    r.pfilt = g.pfilt; r.pfmask = g.pfmask;
     r.ex_own = nullptr; r.ex_rev = nullptr;
     return r;
 }
@@ -346,11 +353,20 @@ __host__ __device__ __forceinline__ uint64_t draw(uint64_t seed, uint64_t k, uin
 }
 
 // the time-sorted segment [a, b) of pair (u, v) in the pair view, by one hash lookup
+// (after the pair filter, which answers most lookups of absent pairs from L2)
 template <typename TT>
 __device__ __forceinline__ bool pair_segment(const GraphDevT<TT>& G, int32_t u, int32_t v, int64_t& a,
-                                             int64_t& b) {
+                                             int64_t& b, bool filter = true) {
     unsigned long long key = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
-    unsigned long long h = sm64_mix(key) & G.hmask;
+    unsigned long long h0 = sm64_mix(key);
+    if (filter && G.pfilt) {   // callers that know the pair exists skip the filter
+        uint32_t w = __ldg(G.pfilt + ((h0 >> 32) & G.pfmask));
+        if (!((w >> (h0 & 31)) & (w >> ((h0 >> 5) & 31)) & 1u)) {
+            a = b = 0;
+            return false;
+        }
+    }
+    unsigned long long h = h0 & G.hmask;
     for (unsigned long long it = 0; it <= G.hmask; it++) {
         ulonglong2 sl = __ldg(reinterpret_cast<const ulonglong2*>(G.hslots) + h);
         if (sl.x == key) {
