@@ -220,7 +220,7 @@ int tm_run_batch(const tm_graph* g, const tm_query* queries, int32_t n_queries,
  * serialise them.  Errors: TM_EINVAL, TM_ENOMEM, TM_ECUDA, TM_EOVERFLOW;
  * tm_last_error is not updated. */
 #define TM_NOALLOC_MAX_EDGES 262144
-#define TM_NOALLOC_SCRATCH_BYTES 7346944
+#define TM_NOALLOC_SCRATCH_BYTES 7347200
 int tm_count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, void* stream,
                            int64_t* count);
 

@@ -41,7 +41,7 @@ constexpr double kFullScanP = 0.25;              // keep rate from which windows
 constexpr int64_t kRevMinLen = 8;                // shortest second-edge range worth closing from the other side
 
 // per-window accumulator fields
-enum { A_COUNT = 0, A_WLO, A_WHI, A_FIRST, A_CAND, A_LAST, A_INST, A_N };
+enum { A_COUNT = 0, A_WLO, A_WHI, A_FIRST, A_CAND, A_LAST, A_INST, A_X0, A_X1, A_X2, A_N };
 
 struct WinDev {
     int64_t* lo;      // first edges of the window: positions [lo, hi) of the query's order
@@ -131,6 +131,17 @@ __device__ __forceinline__ int64_t pair_count(const GraphDevT<TT>& G, int32_t u,
     int64_t lo = upper_bound_i64(G.pair_t, a, b, tprev);
     int64_t hi = gallop_ub(G.pair_t, lo, b, thi);
     return hi - lo;
+}
+
+// the same entries as a range [lo, hi) of pair_t (empty: lo == hi)
+template <typename TT>
+__device__ __forceinline__ void pair_range(const GraphDevT<TT>& G, int32_t u, int32_t v, int64_t tprev,
+                                           int64_t thi, int64_t& lo, int64_t& hi) {
+    int64_t a, b;
+    lo = hi = 0;
+    if (thi <= tprev || !pair_segment(G, u, v, a, b)) return;
+    lo = upper_bound_i64(G.pair_t, a, b, tprev);
+    hi = gallop_ub(G.pair_t, lo, b, thi);
 }
 
 // candidates of motif edge P given the bound nodes: entries [lo, lo+len) of
@@ -325,6 +336,24 @@ __device__ __forceinline__ void add_weight(Acc& a, const QPlan& Q, int64_t dur) 
     unsigned long long s = a.f[A_WLO] + wf;
     a.f[A_WHI] += wi + (s < wf ? 1ull : 0ull);
     a.f[A_WLO] = s;
+}
+
+// exact queries counted alongside at smaller spans: cnt instances whose last edge is at t3
+__device__ __forceinline__ void add_sub_at(Acc& a, const QPlan& Q, int64_t t1, int64_t t3,
+                                           unsigned long long cnt) {
+#pragma unroll
+    for (int i = 0; i < kMaxSub; i++)
+        if (i < Q.nsub && t3 - t1 <= Q.dsub[i]) a.f[A_X0 + i] += cnt;
+}
+
+// ... and the instances closed by entries (tc, t1 + dsub_i] of a time-sorted range [lo, hi)
+// whose entries after tc start at lo
+template <typename TT>
+__device__ __forceinline__ void add_sub_range(Acc& a, const QPlan& Q, const TT* __restrict__ ta, int64_t lo,
+                                              int64_t hi, int64_t t1) {
+#pragma unroll
+    for (int i = 0; i < kMaxSub; i++)
+        if (i < Q.nsub) a.f[A_X0 + i] += gallop_ub(ta, lo, hi, t1 + Q.dsub[i]) - lo;
 }
 
 // n instances of duration dur at once: n * (wi + wf 2^-64), exactly as n single adds
@@ -598,8 +627,13 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                     int64_t le2 = mid_rev ? rev_ub - ra : own_ub - pa;   // middle-pair edges at or before t1
                     if (Q.mode == TM_MODE_EXACT) {
                         const int64_t* S = mid_rev == last_rev ? G.ex_own : G.ex_rev;
-                        acc.f[A_COUNT] += (unsigned long long)((__ldg(S + hh) - __ldg(S + ha)) - (hh - ha) * le2);
+                        int64_t sa = __ldg(S + ha);
+                        acc.f[A_COUNT] += (unsigned long long)((__ldg(S + hh) - sa) - (hh - ha) * le2);
                         acc.f[A_LAST] += 1;
+                        for (int i = 0; i < Q.nsub; i++) {   // exact queries at smaller spans
+                            int64_t hi = gallop_ub(G.pair_t, ha, hh, t1 + Q.dsub[i]);
+                            acc.f[A_X0 + i] += (unsigned long long)((__ldg(S + hi) - sa) - (hi - ha) * le2);
+                        }
                     } else {
                         len = hh - ha;   // items: the last edges; k_match reads ha and le2
                         hh = le2;
@@ -949,6 +983,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     if (cnt) {
                         acc.f[A_COUNT] += cnt;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                        if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
                     }
                 } else if (l2 < 0) {
                     // closing-edge candidate e3 = (x, t3); count second edges in (t1, t3)
@@ -968,6 +1003,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                         if (cnt) {
                             acc.f[A_COUNT] += cnt;
                             if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                            if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
                         }
                     }
                 } else {
@@ -991,10 +1027,16 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     const LevelPlan L = Q.lv[2];
                     if (ok && Q.l == 3 && Q.mode == TM_MODE_EXACT && L.view == kPair) {
                         // close the instance here: the last edge is counted by range length
-                        int64_t cnt = Q.hoist ? hh - upper_bound_i64(G.pair_t, ha, hh, tc)
-                                              : pair_count(G, phi_get(phi, L.su), phi_get(phi, L.sv), tc, thi);
-                        acc.f[A_COUNT] += cnt;
+                        int64_t clo, chi;
+                        if (Q.hoist) {
+                            clo = upper_bound_i64(G.pair_t, ha, hh, tc);
+                            chi = hh;
+                        } else {
+                            pair_range(G, phi_get(phi, L.su), phi_get(phi, L.sv), tc, thi, clo, chi);
+                        }
+                        acc.f[A_COUNT] += chi - clo;
                         acc.f[A_LAST] += 1;
+                        if (Q.nsub && chi > clo) add_sub_range(acc, Q, G.pair_t, clo, chi, t1);
                     } else {
                         deeper = ok;
                     }
@@ -1011,7 +1053,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
 
 // per query: sums over its windows, per shift; Z_k and the mean (Algorithm 1)
 __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __restrict__ res,
-                       ShiftSums* __restrict__ sums) {
+                       ShiftSums* __restrict__ sums, unsigned long long* __restrict__ subc) {
     int qi = blockIdx.x;
     const QPlan& Q = plans[qi];
     __shared__ double sh_d[2][32];
@@ -1093,6 +1135,11 @@ __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __r
             wm2 += dz * (zk - wmean);
         }
         __syncthreads();
+    }
+    if (threadIdx.x == 0 && subc) {
+        // counts of the exact queries at smaller spans (one window: the whole graph)
+        const unsigned long long* a = W.acc + Q.win_base * A_N;
+        for (int i = 0; i < kMaxSub; i++) subc[qi * kMaxSub + i] = (Q.l > 0 && i < Q.nsub) ? a[A_X0 + i] : 0;
     }
     if (threadIdx.x == 0) {
         tm_result r;
@@ -1346,6 +1393,11 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 P.own_hi = S.own_hi;
             }
         }
+        if (dbg && dbg->nsub && hp[(size_t)i].mode == TM_MODE_EXACT) {
+            QPlan& P = hp[(size_t)i];
+            P.nsub = std::min(dbg->nsub[i], (int32_t)kMaxSub);
+            for (int x = 0; x < P.nsub; x++) P.dsub[x] = dbg->sub_delta[(size_t)i * kMaxSub + x];
+        }
         hp[(size_t)i].win_base = NW;
         hp[(size_t)i].sum_base = n_sums;
         n_sums += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].b;
@@ -1367,7 +1419,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
-                a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
+                a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1)) +
+                a256(8 * kMaxSub * (size_t)nq);
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
     char* p = sb;
@@ -1406,6 +1459,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     int64_t* dW2 = (int64_t*)take(8);
     unsigned long long* dctr = (unsigned long long*)take(8);
     ShiftSums* dsums = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
+    unsigned long long* dsubc = (unsigned long long*)take(8 * kMaxSub * (size_t)nq);
 
     int rc = TM_OK;
     auto fail = [&](cudaError_t e, const char* what) {
@@ -1525,12 +1579,17 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     if (rc == TM_OK) {
         int ev_f0 = pe.mark(st);
-        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, dbg && dbg->sums ? dsums : nullptr); count_launch();
+        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, dbg && dbg->sums ? dsums : nullptr,
+                                   dbg && dbg->sub_count ? dsubc : nullptr);
+        count_launch();
         fail(cudaGetLastError(), "k_fold");
         ev_f1 = pe.mark(st);
         if (ev_m1 < 0) ev_m1 = ev_f0;
     }
     if (rc == TM_OK) fail(cudaMemcpyAsync(res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
+    if (rc == TM_OK && dbg && dbg->sub_count)
+        fail(cudaMemcpyAsync(dbg->sub_count, dsubc, 8 * kMaxSub * (size_t)nq, cudaMemcpyDeviceToHost, st),
+             "span counts");
     if (rc == TM_OK && dbg && dbg->sums && n_sums > 0) {
         std::memset(dbg->sums, 0, sizeof(ShiftSums) * (size_t)n_sums);   // rejected queries write none
         fail(cudaMemcpyAsync(dbg->sums, dsums, sizeof(ShiftSums) * (size_t)n_sums, cudaMemcpyDeviceToHost, st),
@@ -1608,10 +1667,86 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
 
 namespace {
 
-int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
-                   BatchOut* dbg) {
+int run_batch_typed(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
+                    BatchOut* dbg) {
     if (g && g->dev.tbytes == 4) return run_batch_t<int32_t>(g, qs, nq, res, st, dbg);
     return run_batch_t<int64_t>(g, qs, nq, res, st, dbg);
+}
+
+// exact three-edge queries whose last edge joins two bound nodes: a query of the same
+// motif at a smaller span counts a subset of the same enumeration (the instances whose
+// duration is within its span), so it rides along with the largest span's query
+bool same_motif(const tm_motif* a, const tm_motif* b) {
+    if (a == b) return true;
+    if (a->l != b->l || a->k != b->k) return false;
+    return std::memcmp(a->lv, b->lv, sizeof(LevelPlan) * (size_t)a->l) == 0;
+}
+
+int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
+                   BatchOut* dbg) {
+    if (dbg || !g || !qs || !res || nq < 2) return run_batch_typed(g, qs, nq, res, st, dbg);
+    std::vector<int> lead((size_t)nq, -1), slot((size_t)nq, -1);   // span members: their leader
+    std::vector<std::vector<int>> groups;
+    for (int i = 0; i < nq; i++) {
+        const tm_query& q = qs[i];
+        std::string why;
+        if (q.mode != TM_MODE_EXACT || !q.motif || q.motif->l != 3 || q.motif->lv[2].view != kPair) continue;
+        if (validate_query(g, q, why) != TM_OK) continue;
+        bool placed = false;
+        for (auto& gr : groups)
+            if ((int)gr.size() < 1 + kMaxSub && same_motif(qs[gr[0]].motif, q.motif)) {
+                gr.push_back(i);
+                placed = true;
+                break;
+            }
+        if (!placed) groups.push_back({i});
+    }
+    bool any = false;
+    for (auto& gr : groups) {
+        if (gr.size() < 2) continue;
+        any = true;
+        int L = gr[0];
+        for (int i : gr)
+            if (qs[i].delta > qs[L].delta) L = i;
+        int k = 0;
+        for (int i : gr)
+            if (i != L) { lead[(size_t)i] = L; slot[(size_t)i] = k++; }
+    }
+    if (!any) return run_batch_typed(g, qs, nq, res, st, nullptr);
+    // the batch without the members, each leader carrying its members' spans
+    std::vector<tm_query> qc;
+    std::vector<int> pos((size_t)nq, -1);
+    for (int i = 0; i < nq; i++)
+        if (lead[(size_t)i] < 0) { pos[(size_t)i] = (int)qc.size(); qc.push_back(qs[i]); }
+    int nc = (int)qc.size();
+    std::vector<int32_t> nsub((size_t)nc, 0);
+    std::vector<int64_t> sd((size_t)nc * kMaxSub, 0);
+    for (int i = 0; i < nq; i++) {
+        if (lead[(size_t)i] < 0) continue;
+        int c = pos[(size_t)lead[(size_t)i]];
+        sd[(size_t)c * kMaxSub + slot[(size_t)i]] = qs[i].delta;
+        nsub[(size_t)c] = std::max(nsub[(size_t)c], slot[(size_t)i] + 1);
+    }
+    std::vector<tm_result> rc_res((size_t)nc);
+    std::vector<unsigned long long> sc((size_t)nc * kMaxSub, 0);
+    BatchOut bo;
+    bo.nsub = nsub.data();
+    bo.sub_delta = sd.data();
+    bo.sub_count = sc.data();
+    int rc = run_batch_typed(g, qc.data(), nc, rc_res.data(), st, &bo);
+    for (int i = 0; i < nq; i++) {
+        if (lead[(size_t)i] < 0) {
+            res[i] = rc_res[(size_t)pos[(size_t)i]];
+            continue;
+        }
+        int c = pos[(size_t)lead[(size_t)i]];
+        tm_result r = rc_res[(size_t)c];   // status of the shared enumeration
+        r.count = (int64_t)sc[(size_t)c * kMaxSub + slot[(size_t)i]];
+        r.estimate = (double)r.count;
+        r.first_edges = r.cand_edges = r.last_ranges = r.inst_read = 0;   // the work is the leader's
+        res[i] = r;
+    }
+    return rc;
 }
 
 // TM_Q_AUTO: p from a pilot estimate (see tm.h): the smallest p whose sampling standard
@@ -1681,10 +1816,10 @@ int count_plain_t(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* 
     TM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     char* sb = nullptr;
     int rc = TM_OK;
-    static_assert(sizeof(QPlan) <= 256, "the plan and the counter share a 512-byte block");
-    cudaError_t e = cudaMallocAsync((void**)&sb, 512, st);
+    static_assert(sizeof(QPlan) <= 512, "the plan and the counter share a 768-byte block");
+    cudaError_t e = cudaMallocAsync((void**)&sb, 768, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sb, &P, sizeof(P), cudaMemcpyHostToDevice, st);
-    unsigned long long* dc = (unsigned long long*)(sb + 256);
+    unsigned long long* dc = (unsigned long long*)(sb + 512);
     if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, 8, st);
     if (e == cudaSuccess && g->m > 0) {
         int nsm = sm_count();
@@ -1853,7 +1988,7 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
     }
-    k_fold<<<1, 256, 0, st>>>(dplan, W, dres, nullptr); count_launch();
+    k_fold<<<1, 256, 0, st>>>(dplan, W, dres, nullptr, nullptr); count_launch();
     e = cudaGetLastError();
     tm_result hres;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st);
@@ -2080,7 +2215,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         }
     }
     if (rc == TM_OK) {
-        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, nullptr); count_launch();
+        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, nullptr, nullptr); count_launch();
         fail(cudaGetLastError(), "k_fold");
     }
     fail(cudaMemcpyAsync(b->h_res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");

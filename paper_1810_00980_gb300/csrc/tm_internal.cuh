@@ -201,8 +201,14 @@ struct QPlan {
     int64_t own_hi;
     int64_t m_total;     // |T| in q_j = r |T_j| / |T|
     int64_t sum_base;    // first per-shift sums slot of this query
+    // exact three-edge queries of the same motif at smaller spans, counted in the same
+    // enumeration (spans dsub[0..nsub) < delta; their counts go to the A_X* accumulators)
+    int32_t nsub;
+    int32_t pad3;
+    int64_t dsub[3];
     LevelPlan lv[TM_L_MAX];
 };
+constexpr int kMaxSub = 3;
 
 struct Tuning {
     int block_threads = 256;
@@ -236,6 +242,9 @@ struct BatchOut {                 // optional per-window readback for one query
     int64_t shift = 0;
     const SegSpec* seg = nullptr; // per query, or null (whole graph)
     ShiftSums* sums = nullptr;    // host: per query, per shift (exact: one), or null
+    const int32_t* nsub = nullptr;            // per query: spans counted alongside (exact)
+    const int64_t* sub_delta = nullptr;       // [nq][kMaxSub]
+    unsigned long long* sub_count = nullptr;  // host out: [nq][kMaxSub]
 };
 
 int run_batch(const tm_graph* g, const tm_query* qs, int nq, tm_result* res,

@@ -603,3 +603,31 @@ def test_auto_p_meets_target_on_most_seeds(tm):
     res = tm.run_batch(g, qs)
     errs = [abs(r["estimate"] - exact) / exact for r in res]
     assert sum(e <= 0.10 for e in errs) >= 16, errs
+
+
+def test_exact_spans_ride_along_in_one_enumeration(tm, orc):
+    """Exact three-edge queries of one motif at several spans share the largest span's
+    enumeration (each instance also counted for every span its duration fits): counts
+    equal the single-query counts and the oracle's; the members report no work."""
+    src, dst, t = synth.chung_lu_hawkes(2000, 100_000, 2.1, seed=7, horizon=3_000_000,
+                                        max_degree=20_000, hub_bursts=6, burst_max=400)
+    g = _graph(tm, src, dst, t)
+    names = ("cycle3", "outstar3", "pingpong", "cycle4")
+    qs, want = [], []
+    for n in names:
+        ms, md = synth.MOTIFS[n]
+        mo = tm.Motif(ms, md)
+        for d in (86400, 600, 3600, 3600, 0, 7):
+            qs.append(tm.exact_query(mo, d))
+            want.append(orc.count_exact(src, dst, t, ms, md, d, threads=8))
+    mo2 = tm.Motif([2, 2, 2], [0, 1, 0])          # the same motif through another handle
+    qs.append(tm.exact_query(mo2, 1800))
+    want.append(orc.count_exact(src, dst, t, [2, 2, 2], [0, 1, 0], 1800, threads=8))
+    res = tm.run_batch(g, qs)
+    for q, r, w in zip(qs, res, want):
+        assert r["status"] == 0 and r["count"] == w, (q.delta, r["count"], w)
+        assert r["count"] == tm.run_batch(g, [q])[0]["count"]
+    # per motif at most one query did the work (the largest span); four-edge motifs are alone
+    for k, n in enumerate(names[:3]):
+        worked = [r["first_edges"] > 0 for r in res[6 * k:6 * k + 6]]
+        assert sum(worked) <= 2 and worked[0]   # groups of at most four queries
