@@ -201,18 +201,28 @@ __global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t* __restrict_
 // Stable scatter of one tile: warp w owns items [w*512, w*512+512) of the
 // tile, taken 32 at a time in index order; ranks among equal digits come from
 // __match_any_sync and per-warp running counters, then warps are offset by
-// the counts of lower warps.
+// the counts of lower warps.  The tile is first reordered by digit in shared
+// memory, so that neighbouring threads write neighbouring addresses of one
+// digit's output run (coalesced) instead of scattering single words.
+// Dynamic shared memory: kSortTile keys and values, per-warp digit counters,
+// and per-digit tile starts and output bases (sort_smem_bytes(db)).
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
                 int db, const int64_t* __restrict__ offs, int64_t ntiles) {
-    __shared__ int32_t cnt[kSortWarps][1 << kMaxDigitBits];
+    extern __shared__ __align__(16) unsigned char sm_sort[];
     int nd = 1 << db;
+    uint32_t* skey = (uint32_t*)sm_sort;                        // [kSortTile]
+    uint32_t* sval = skey + kSortTile;                          // [kSortTile]
+    int64_t* gbase = (int64_t*)(sval + kSortTile);              // [nd] output index of tile slot 0 of digit d
+    int32_t* cnt = (int32_t*)(gbase + nd);                      // [kSortWarps][nd]
+    int32_t* tds = cnt + kSortWarps * nd;                       // [nd] tile start of digit d
     uint32_t mask = (uint32_t)nd - 1;
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = lane; i < nd; i += 32) cnt[w][i] = 0;
+    for (int i = lane; i < nd; i += 32) cnt[w * nd + i] = 0;
     __syncwarp();
-    int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * (kSortItems * 32);
+    int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    int64_t base = tbase + (int64_t)w * (kSortItems * 32);
     uint32_t key[kSortItems], val[kSortItems];
     int32_t rank[kSortItems];
     unsigned lt = (1u << lane) - 1u;
@@ -225,34 +235,75 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
         uint32_t d = ok ? ((key[r] >> shift) & mask) : 0xffffffffu;
         unsigned peers = __match_any_sync(kFull, d);
         int before = __popc(peers & lt);
-        int32_t c0 = ok ? cnt[w][d] : 0;
+        int32_t c0 = ok ? cnt[w * nd + d] : 0;
         rank[r] = c0 + before;
         __syncwarp();
         int leader = 31 - __clz(peers);
-        if (ok && lane == leader) cnt[w][d] = c0 + __popc(peers);
+        if (ok && lane == leader) cnt[w * nd + d] = c0 + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
+    // per digit: warp offsets inside the digit, the digit's total in tds (scanned below)
     for (int d = threadIdx.x; d < nd; d += blockDim.x) {
         int32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < kSortWarps; ww++) {
-            int32_t c = cnt[ww][d];
-            cnt[ww][d] = run;
+            int32_t c = cnt[ww * nd + d];
+            cnt[ww * nd + d] = run;
             run += c;
+        }
+        tds[d] = run;
+    }
+    __syncthreads();
+    if (w == 0) {   // exclusive scan of the digit totals (nd <= 1024: 32 per lane at most)
+        int per = (nd + 31) / 32;
+        int32_t sum = 0;
+        for (int i = 0; i < per; i++) {
+            int d = lane * per + i;
+            if (d < nd) sum += tds[d];
+        }
+        int32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        int32_t run = inc - sum;
+        for (int i = 0; i < per; i++) {
+            int d = lane * per + i;
+            if (d < nd) {
+                int32_t c = tds[d];
+                tds[d] = run;
+                run += c;
+            }
         }
     }
     __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x)
+        gbase[d] = offs[(int64_t)d * ntiles + blockIdx.x] - tds[d];
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
         int64_t idx = base + r * 32 + lane;
         if (idx < n) {
             uint32_t d = (key[r] >> shift) & mask;
-            int64_t pos = offs[(int64_t)d * ntiles + blockIdx.x] + cnt[w][d] + rank[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            int32_t lp = tds[d] + cnt[w * nd + d] + rank[r];
+            skey[lp] = key[r];
+            sval[lp] = val[r];
         }
     }
+    __syncthreads();
+    int64_t tn = min((int64_t)kSortTile, n - tbase);
+    for (int i = threadIdx.x; i < tn; i += blockDim.x) {
+        uint32_t k = skey[i];
+        int64_t pos = gbase[(k >> shift) & mask] + i;
+        kout[pos] = k;
+        vout[pos] = sval[i];
+    }
+}
+
+size_t sort_smem_bytes(int db) {
+    size_t nd = (size_t)1 << db;
+    return 2 * 4 * (size_t)kSortTile + 8 * nd + 4 * nd * (kSortWarps + 1);
 }
 
 }  // namespace
@@ -355,6 +406,20 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_
     if (n <= 1 || bits <= 0) return TM_OK;
     int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
     int db = (bits + passes - 1) / passes;
+    {
+        // the scatter's dynamic shared memory can exceed the 48 KB default: allow the
+        // largest digit width once per device
+        static std::mutex mu;
+        static bool done[64] = {};
+        int dev = 0;
+        TM_CUDA(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && !done[dev]) {
+            TM_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sort_smem_bytes(kMaxDigitBits)));
+            done[dev] = true;
+        }
+    }
     int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     int64_t nh = ((int64_t)1 << db) * ntiles;
     int32_t* hist = nullptr;
@@ -372,8 +437,9 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_
         k_i32_to_i64<<<(unsigned)((nhp + 255) / 256 < 4096 ? (nhp + 255) / 256 : 4096), 256, 0, st>>>(hist, hist64, nhp); count_launch();
         rc = scan_exclusive_i64(hist64, offs, nhp, nullptr, st);
         if (rc != TM_OK) break;
-        k_radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, width,
-                                                                  offs, ntiles); count_launch();
+        k_radix_scatter<<<(unsigned)ntiles, kSortThreads, sort_smem_bytes(width), st>>>(ka, va, kb, vb, n, shift,
+                                                                                       width, offs, ntiles);
+        count_launch();
         if (cudaGetLastError() != cudaSuccess) { rc = TM_ECUDA; break; }
         uint32_t* t;
         t = ka; ka = kb; kb = t;
