@@ -105,6 +105,76 @@ __global__ void k_pair_heads(const uint32_t* __restrict__ perm, const int32_t* _
     }
 }
 
+// ---- views for 32-bit times: each sort carries its payload (the other endpoint and the
+// time packed in 64 bits) instead of an edge index, so no view is gathered through a
+// permutation (random reads of the edge arrays) after the sort
+__global__ void k_ingest_kv(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                            const int64_t* __restrict__ t, int64_t m, int64_t tmin,
+                            int32_t* __restrict__ gs, int32_t* __restrict__ gd, int32_t* __restrict__ gt,
+                            uint32_t* __restrict__ key_src, uint32_t* __restrict__ key_dst,
+                            uint64_t* __restrict__ pay_out, uint64_t* __restrict__ pay_in) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = src[i], d = dst[i];
+        uint32_t tt = (uint32_t)(t[i] - tmin);
+        gs[i] = s;
+        gd[i] = d;
+        gt[i] = (int32_t)tt;
+        key_src[i] = (uint32_t)s;
+        key_dst[i] = (uint32_t)d;
+        pay_out[i] = (uint64_t)(uint32_t)d | ((uint64_t)tt << 32);
+        pay_in[i] = (uint64_t)(uint32_t)s | ((uint64_t)tt << 32);
+    }
+}
+
+// a sorted view's neighbour and time arrays from its payload
+__global__ void k_split_view(const uint64_t* __restrict__ pay, int64_t m, int32_t* __restrict__ nbr,
+                             int32_t* __restrict__ tv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t v = pay[i];
+        nbr[i] = (int32_t)(uint32_t)v;
+        tv[i] = (int32_t)(uint32_t)(v >> 32);
+    }
+}
+
+// the in view as sort input for the pair view: key = source, payload = destination | time
+__global__ void k_pair_keys(const int32_t* __restrict__ in_nbr, const uint32_t* __restrict__ in_dst,
+                            const int32_t* __restrict__ in_t, int64_t m, uint32_t* __restrict__ key,
+                            uint64_t* __restrict__ pay) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        key[i] = (uint32_t)in_nbr[i];
+        pay[i] = (uint64_t)in_dst[i] | ((uint64_t)(uint32_t)in_t[i] << 32);
+    }
+}
+
+// pair view from (source, destination | time) sorted by source: times, head flags
+__global__ void k_pair_heads_kv(const uint32_t* __restrict__ key, const uint64_t* __restrict__ pay,
+                                int64_t m, int64_t* __restrict__ head, int32_t* __restrict__ pair_t) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t v = pay[i];
+        pair_t[i] = (int32_t)(uint32_t)(v >> 32);
+        head[i] = (i == 0 || key[i] != key[i - 1] || (uint32_t)v != (uint32_t)pay[i - 1]) ? 1 : 0;
+    }
+}
+
+__global__ void k_pair_index_kv(const uint32_t* __restrict__ key, const uint64_t* __restrict__ pay,
+                                const int64_t* __restrict__ head, const int64_t* __restrict__ pid_excl,
+                                int64_t m, int32_t* __restrict__ pair_dst, int64_t* __restrict__ pair_off,
+                                int32_t* __restrict__ pair_src) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (head[i]) {
+            int64_t p = pid_excl[i];
+            pair_dst[p] = (int32_t)(uint32_t)pay[i];
+            pair_off[p] = i;
+            pair_src[p] = (int32_t)key[i];
+        }
+    }
+}
+
 // pid_excl[i] = number of heads before i; a head at i starts pair pid_excl[i]
 __global__ void k_pair_index(const uint32_t* __restrict__ perm, const int32_t* __restrict__ dst,
                              const int64_t* __restrict__ head, const int64_t* __restrict__ pid_excl,
@@ -296,7 +366,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     // ---- scratch: keys/values for three sorts (double-buffered) + pair scan
     uint32_t *ks, *kd, *va, *vb, *kt, *vt;
     int64_t *head, *pid, *dP;
-    size_t scratch = 6 * align256(4 * M) + 2 * sz_i64m + 256;
+    // index path: 6 u32 + 2 i64 per edge; payload path (32-bit times): 3 u32 + 3 u64
+    size_t scratch = std::max(6 * align256(4 * M) + 2 * sz_i64m, 3 * align256(4 * M) + 3 * sz_i64m) + 256;
     char* sb = nullptr;
     e = cudaMallocAsync((void**)&sb, scratch, st);
     if (e != cudaSuccess) {
@@ -315,7 +386,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     vt = (uint32_t*)takes(4 * M);
     head = (int64_t*)takes(8 * M);
     pid = (int64_t*)takes(8 * M);
-    dP = (int64_t*)takes(8);
+    dP = (int64_t*)(sb + scratch - 256);
 
     int bits = bits_for(n);
     unsigned gr = grid_for(m);
@@ -335,44 +406,105 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         if (tb == 4) typed_launch(int32_t{}, which, perm, other, nbr, tv);
         else typed_launch(int64_t{}, which, perm, other, nbr, tv);
     };
-    tlaunch(0, nullptr, nullptr, nullptr, nullptr);
-    if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
-    // out view: edges stably sorted by source (time order kept inside a source)
-    if (rc == TM_OK) rc = radix_sort_pairs(ks, va, kt, vt, m, bits, st);
-    if (rc == TM_OK) {
-        k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(ks, m, n, out_off); count_launch();
-        tlaunch(1, va, gd, out_nbr, out_t);
+    uint32_t* psrc = nullptr;   // pair sources (the hash keys), in pair order
+    if (tb == 4) {
+        // payload path: scratch laid out as three u32 and three u64 arrays
+        char* q2 = sb;
+        auto take2 = [&](size_t bytes) { char* r = q2; q2 += align256(bytes); return (void*)r; };
+        uint32_t* k0 = (uint32_t*)take2(4 * M);
+        uint32_t* k1 = (uint32_t*)take2(4 * M);
+        uint32_t* k2 = (uint32_t*)take2(4 * M);
+        uint64_t* p0 = (uint64_t*)take2(8 * M);
+        uint64_t* p1 = (uint64_t*)take2(8 * M);
+        uint64_t* p2 = (uint64_t*)take2(8 * M);
+        uint32_t* kr = nullptr;
+        uint64_t* pr = nullptr;
+        k_ingest_kv<<<gr, kThreads, 0, st>>>(d_src, d_dst, d_t, m, tmin, gs, gd, (int32_t*)gt, k0, k1, p0, p1);
+        count_launch();
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
-        if (rc == TM_OK && cudaMemcpyAsync(out_src, ks, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            rc = TM_ECUDA;
-    }
-    // in view: stably sorted by destination
-    if (rc == TM_OK) rc = radix_sort_pairs(kd, vb, kt, vt, m, bits, st);
-    if (rc == TM_OK) {
-        k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kd, m, n, in_off); count_launch();
-        tlaunch(1, vb, gs, in_nbr, in_t);
+        // out view: (source; destination | time) stably sorted by source
+        if (rc == TM_OK) rc = radix_sort_kv64(k0, p0, k2, p2, m, bits, st, &kr, &pr);
+        if (rc == TM_OK) {
+            k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kr, m, n, out_off); count_launch();
+            k_split_view<<<gr, kThreads, 0, st>>>(pr, m, out_nbr, (int32_t*)out_t); count_launch();
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+            if (rc == TM_OK && cudaMemcpyAsync(out_src, kr, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                rc = TM_ECUDA;
+        }
+        // in view: (destination; source | time) stably sorted by destination
+        if (rc == TM_OK) rc = radix_sort_kv64(k1, p1, k0, p0, m, bits, st, &kr, &pr);
+        if (rc == TM_OK) {
+            k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kr, m, n, in_off); count_launch();
+            k_split_view<<<gr, kThreads, 0, st>>>(pr, m, in_nbr, (int32_t*)in_t); count_launch();
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+            if (rc == TM_OK && cudaMemcpyAsync(in_dst, kr, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                rc = TM_ECUDA;
+        }
+        // pair view: the in view stably re-sorted by source = (source, destination, time)
+        if (rc == TM_OK) {
+            k_pair_keys<<<gr, kThreads, 0, st>>>(in_nbr, (const uint32_t*)in_dst, (const int32_t*)in_t, m, k2, p2);
+            count_launch();
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        }
+        if (rc == TM_OK) rc = radix_sort_kv64(k2, p2, k0, p0, m, bits, st, &kr, &pr);
+        // heads and pair indices in the u64 arrays the sort left free; sources in a free u32 one
+        int64_t* hd = (int64_t*)p1;
+        int64_t* pd = (int64_t*)(pr == p2 ? p0 : p2);
+        psrc = kr == k2 ? k0 : k2;
+        if (rc == TM_OK) {
+            k_pair_heads_kv<<<gr, kThreads, 0, st>>>(kr, pr, m, hd, (int32_t*)pair_t); count_launch();
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        }
+        if (rc == TM_OK) rc = scan_exclusive_i64(hd, pd, m, dP, st);
+        if (rc == TM_OK) {
+            k_pair_index_kv<<<gr, kThreads, 0, st>>>(kr, pr, hd, pd, m, pair_dst, pair_off, (int32_t*)psrc);
+            count_launch();
+            k_pair_tail<<<1, 1, 0, st>>>(pair_off, dP, m); count_launch();
+            k_pk_off<<<grid_for((int64_t)n + 1), kThreads, 0, st>>>(out_off, hd, pd, dP, m, n, pk_off); count_launch();
+            k_pair_pid<<<gr, kThreads, 0, st>>>(hd, pd, m, pair_pid); count_launch();
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        }
+    } else {
+        tlaunch(0, nullptr, nullptr, nullptr, nullptr);
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
-        if (rc == TM_OK && cudaMemcpyAsync(in_dst, kd, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            rc = TM_ECUDA;
-    }
-    // pair view: the in-view order stably re-sorted by source = (src, dst, time)
-    if (rc == TM_OK) {
-        tlaunch(1, vb, gs, (int32_t*)ks, head);   // sources in in-view order; times go to scratch
-        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
-    }
-    if (rc == TM_OK) rc = radix_sort_pairs(ks, vb, kt, vt, m, bits, st);
-    if (rc == TM_OK) {
-        tlaunch(2, vb, nullptr, nullptr, pair_t);
-        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
-    }
-    if (rc == TM_OK) rc = scan_exclusive_i64(head, pid, m, dP, st);
-    if (rc == TM_OK) {
-        k_pair_index<<<gr, kThreads, 0, st>>>(vb, gd, head, pid, m, pair_dst, pair_off); count_launch();
-        k_pair_tail<<<1, 1, 0, st>>>(pair_off, dP, m); count_launch();
-        k_pk_off<<<grid_for((int64_t)n + 1), kThreads, 0, st>>>(out_off, head, pid, dP, m, n, pk_off); count_launch();
-        k_pair_src<<<gr, kThreads, 0, st>>>(vb, gs, head, pid, m, (int32_t*)kt); count_launch();
-        k_pair_pid<<<gr, kThreads, 0, st>>>(head, pid, m, pair_pid); count_launch();
-        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        // out view: edges stably sorted by source (time order kept inside a source)
+        if (rc == TM_OK) rc = radix_sort_pairs(ks, va, kt, vt, m, bits, st);
+        if (rc == TM_OK) {
+            k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(ks, m, n, out_off); count_launch();
+            tlaunch(1, va, gd, out_nbr, out_t);
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+            if (rc == TM_OK && cudaMemcpyAsync(out_src, ks, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                rc = TM_ECUDA;
+        }
+        // in view: stably sorted by destination
+        if (rc == TM_OK) rc = radix_sort_pairs(kd, vb, kt, vt, m, bits, st);
+        if (rc == TM_OK) {
+            k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kd, m, n, in_off); count_launch();
+            tlaunch(1, vb, gs, in_nbr, in_t);
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+            if (rc == TM_OK && cudaMemcpyAsync(in_dst, kd, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                rc = TM_ECUDA;
+        }
+        // pair view: the in-view order stably re-sorted by source = (src, dst, time)
+        if (rc == TM_OK) {
+            tlaunch(1, vb, gs, (int32_t*)ks, head);   // sources in in-view order; times go to scratch
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        }
+        if (rc == TM_OK) rc = radix_sort_pairs(ks, vb, kt, vt, m, bits, st);
+        if (rc == TM_OK) {
+            tlaunch(2, vb, nullptr, nullptr, pair_t);
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        }
+        if (rc == TM_OK) rc = scan_exclusive_i64(head, pid, m, dP, st);
+        if (rc == TM_OK) {
+            k_pair_index<<<gr, kThreads, 0, st>>>(vb, gd, head, pid, m, pair_dst, pair_off); count_launch();
+            k_pair_tail<<<1, 1, 0, st>>>(pair_off, dP, m); count_launch();
+            k_pk_off<<<grid_for((int64_t)n + 1), kThreads, 0, st>>>(out_off, head, pid, dP, m, n, pk_off); count_launch();
+            k_pair_src<<<gr, kThreads, 0, st>>>(vb, gs, head, pid, m, (int32_t*)kt); count_launch();
+            psrc = kt;
+            k_pair_pid<<<gr, kThreads, 0, st>>>(head, pid, m, pair_pid); count_launch();
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        }
     }
     int64_t P = 0;
     if (rc == TM_OK) {
@@ -399,7 +531,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
             e = cudaMemsetAsync(g->hash_block, 0xff, 16 * cap, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(filt, 0, 4 * fw, st);
             if (e == cudaSuccess) {
-                k_hash_insert<<<grid_for(P), kThreads, 0, st>>>((const int32_t*)kt, pair_dst, pair_off, P,
+                k_hash_insert<<<grid_for(P), kThreads, 0, st>>>((const int32_t*)psrc, pair_dst, pair_off, P,
                                                                (unsigned long long*)g->hash_block, cap - 1,
                                                                filt, fw - 1);
                 count_launch();

@@ -206,14 +206,15 @@ __global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t* __restrict_
 // digit's output run (coalesced) instead of scattering single words.
 // Dynamic shared memory: kSortTile keys and values, per-warp digit counters,
 // and per-digit tile starts and output bases (sort_smem_bytes(db)).
+template <typename V>
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+k_radix_scatter(const uint32_t* __restrict__ kin, const V* __restrict__ vin,
+                uint32_t* __restrict__ kout, V* __restrict__ vout, int64_t n, int shift,
                 int db, const int64_t* __restrict__ offs, int64_t ntiles) {
     extern __shared__ __align__(16) unsigned char sm_sort[];
     int nd = 1 << db;
     uint32_t* skey = (uint32_t*)sm_sort;                        // [kSortTile]
-    uint32_t* sval = skey + kSortTile;                          // [kSortTile]
+    V* sval = (V*)(skey + kSortTile);                           // [kSortTile]
     int64_t* gbase = (int64_t*)(sval + kSortTile);              // [nd] output index of tile slot 0 of digit d
     int32_t* cnt = (int32_t*)(gbase + nd);                      // [kSortWarps][nd]
     int32_t* tds = cnt + kSortWarps * nd;                       // [nd] tile start of digit d
@@ -223,7 +224,7 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
     __syncwarp();
     int64_t tbase = (int64_t)blockIdx.x * kSortTile;
     int64_t base = tbase + (int64_t)w * (kSortItems * 32);
-    uint32_t key[kSortItems], val[kSortItems];
+    uint32_t key[kSortItems];
     int32_t rank[kSortItems];
     unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -231,7 +232,6 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
         int64_t idx = base + r * 32 + lane;
         bool ok = idx < n;
         key[r] = ok ? kin[idx] : 0u;
-        val[r] = ok ? vin[idx] : 0u;
         uint32_t d = ok ? ((key[r] >> shift) & mask) : 0xffffffffu;
         unsigned peers = __match_any_sync(kFull, d);
         int before = __popc(peers & lt);
@@ -288,7 +288,7 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
             uint32_t d = (key[r] >> shift) & mask;
             int32_t lp = tds[d] + cnt[w * nd + d] + rank[r];
             skey[lp] = key[r];
-            sval[lp] = val[r];
+            sval[lp] = vin[idx];   // values are read here, not held through the ranking
         }
     }
     __syncthreads();
@@ -301,9 +301,68 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
     }
 }
 
+template <typename V>
 size_t sort_smem_bytes(int db) {
     size_t nd = (size_t)1 << db;
-    return 2 * 4 * (size_t)kSortTile + 8 * nd + 4 * nd * (kSortWarps + 1);
+    return (4 + sizeof(V)) * (size_t)kSortTile + 8 * nd + 4 * nd * (kSortWarps + 1);
+}
+
+// LSD radix sort of (u32 key, V value) by the low `bits` bits of the key, stable; the
+// sorted arrays end in whichever of (keys, vals) / (keys_tmp, vals_tmp) the last pass
+// wrote, returned through kres / vres
+template <typename V>
+int radix_sort_t(uint32_t* keys, V* vals, uint32_t* keys_tmp, V* vals_tmp, int64_t n, int bits,
+                 cudaStream_t st, uint32_t** kres, V** vres) {
+    *kres = keys;
+    *vres = vals;
+    if (n <= 1 || bits <= 0) return TM_OK;
+    int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    int db = (bits + passes - 1) / passes;
+    {
+        // the scatter's dynamic shared memory can exceed the 48 KB default: allow the
+        // largest digit width once per device and value type
+        static std::mutex mu;
+        static bool done[64] = {};
+        int dev = 0;
+        TM_CUDA(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && !done[dev]) {
+            TM_CUDA(cudaFuncSetAttribute(k_radix_scatter<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sort_smem_bytes<V>(kMaxDigitBits)));
+            done[dev] = true;
+        }
+    }
+    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    int64_t nh = ((int64_t)1 << db) * ntiles;
+    int32_t* hist = nullptr;
+    int64_t* offs = nullptr;
+    TM_CUDA(cudaMallocAsync((void**)&hist, sizeof(int32_t) * (size_t)nh, st));
+    TM_CUDA(cudaMallocAsync((void**)&offs, sizeof(int64_t) * (size_t)nh * 2, st));
+    int64_t* hist64 = offs + nh;
+    uint32_t *ka = keys, *kb = keys_tmp;
+    V *va = vals, *vb = vals_tmp;
+    int rc = TM_OK;
+    for (int p = 0; p < passes && rc == TM_OK; p++) {
+        int shift = p * db;
+        int width = (shift + db > bits) ? bits - shift : db;
+        k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ka, n, shift, width, hist, ntiles); count_launch();
+        int64_t nhp = ((int64_t)1 << width) * ntiles;
+        k_i32_to_i64<<<(unsigned)((nhp + 255) / 256 < 4096 ? (nhp + 255) / 256 : 4096), 256, 0, st>>>(hist, hist64, nhp); count_launch();
+        rc = scan_exclusive_i64(hist64, offs, nhp, nullptr, st);
+        if (rc != TM_OK) break;
+        k_radix_scatter<V><<<(unsigned)ntiles, kSortThreads, sort_smem_bytes<V>(width), st>>>(
+            ka, va, kb, vb, n, shift, width, offs, ntiles);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) { rc = TM_ECUDA; break; }
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(offs, st);
+    if (rc != TM_OK) set_error("radix sort launch failed");
+    *kres = ka;
+    *vres = va;
+    return rc;
 }
 
 }  // namespace
@@ -403,56 +462,18 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_
                      int64_t n, int bits, cudaStream_t st) {
     // Sorts (keys, vals) stably by the low `bits` bits of keys; the result ends
     // in keys/vals.  bits <= 32.
-    if (n <= 1 || bits <= 0) return TM_OK;
-    int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
-    int db = (bits + passes - 1) / passes;
-    {
-        // the scatter's dynamic shared memory can exceed the 48 KB default: allow the
-        // largest digit width once per device
-        static std::mutex mu;
-        static bool done[64] = {};
-        int dev = 0;
-        TM_CUDA(cudaGetDevice(&dev));
-        std::lock_guard<std::mutex> lk(mu);
-        if (dev >= 0 && dev < 64 && !done[dev]) {
-            TM_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sort_smem_bytes(kMaxDigitBits)));
-            done[dev] = true;
-        }
+    uint32_t *kr, *vr;
+    int rc = radix_sort_t<uint32_t>(keys, vals, keys_tmp, vals_tmp, n, bits, st, &kr, &vr);
+    if (rc == TM_OK && kr != keys) {
+        TM_CUDA(cudaMemcpyAsync(keys, kr, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        TM_CUDA(cudaMemcpyAsync(vals, vr, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     }
-    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    int64_t nh = ((int64_t)1 << db) * ntiles;
-    int32_t* hist = nullptr;
-    int64_t* offs = nullptr;
-    TM_CUDA(cudaMallocAsync((void**)&hist, sizeof(int32_t) * (size_t)nh, st));
-    TM_CUDA(cudaMallocAsync((void**)&offs, sizeof(int64_t) * (size_t)nh * 2, st));
-    int64_t* hist64 = offs + nh;
-    uint32_t *ka = keys, *va = vals, *kb = keys_tmp, *vb = vals_tmp;
-    int rc = TM_OK;
-    for (int p = 0; p < passes && rc == TM_OK; p++) {
-        int shift = p * db;
-        int width = (shift + db > bits) ? bits - shift : db;
-        k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ka, n, shift, width, hist, ntiles); count_launch();
-        int64_t nhp = ((int64_t)1 << width) * ntiles;
-        k_i32_to_i64<<<(unsigned)((nhp + 255) / 256 < 4096 ? (nhp + 255) / 256 : 4096), 256, 0, st>>>(hist, hist64, nhp); count_launch();
-        rc = scan_exclusive_i64(hist64, offs, nhp, nullptr, st);
-        if (rc != TM_OK) break;
-        k_radix_scatter<<<(unsigned)ntiles, kSortThreads, sort_smem_bytes(width), st>>>(ka, va, kb, vb, n, shift,
-                                                                                       width, offs, ntiles);
-        count_launch();
-        if (cudaGetLastError() != cudaSuccess) { rc = TM_ECUDA; break; }
-        uint32_t* t;
-        t = ka; ka = kb; kb = t;
-        t = va; va = vb; vb = t;
-    }
-    if (rc == TM_OK && ka != keys) {
-        cudaMemcpyAsync(keys, ka, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(vals, va, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
-    }
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(offs, st);
-    if (rc != TM_OK) set_error("radix sort launch failed");
     return rc;
+}
+
+int radix_sort_kv64(uint32_t* keys, uint64_t* vals, uint32_t* keys_tmp, uint64_t* vals_tmp, int64_t n,
+                    int bits, cudaStream_t st, uint32_t** kres, uint64_t** vres) {
+    return radix_sort_t<uint64_t>(keys, vals, keys_tmp, vals_tmp, n, bits, st, kres, vres);
 }
 
 namespace {

@@ -258,6 +258,10 @@ int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* d_to
                        cudaStream_t st);
 int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                      int64_t n, int bits, cudaStream_t st);
+// the same with 64-bit values; the sorted arrays end in (keys, vals) or (keys_tmp, vals_tmp),
+// returned through kres / vres (no copy back)
+int radix_sort_kv64(uint32_t* keys, uint64_t* vals, uint32_t* keys_tmp, uint64_t* vals_tmp, int64_t n,
+                    int bits, cudaStream_t st, uint32_t** kres, uint64_t** vres);
 // exclusive scan with the tile sums in caller workspace (2 * ceil(n/2048) int64, n <= 2048^2)
 int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,
                           int64_t* ws, int64_t ws_elems, cudaStream_t st);
