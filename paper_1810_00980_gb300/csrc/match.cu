@@ -437,6 +437,13 @@ __global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int 
             k = 0; j = 0; start = 0; lo = 0; hi = G.m; tend = kInf; kept = 1; qj = 1.0;
             W.tlo[w] = 0;
             W.thi[w] = G.m;
+        } else if (Q.wclamp) {
+            // every window kept: one slot per shift over every edge; start holds the shift
+            k = (int32_t)r;
+            j = 0; lo = 0; hi = G.m; tend = kInf; kept = 1; qj = 1.0;
+            start = -(int64_t)(draw(Q.seed, (uint64_t)k, 0) % (uint64_t)Q.cd) - Q.t_off;
+            W.tlo[w] = 0;
+            W.thi[w] = G.m;
         } else {
             k = (int32_t)(r / Q.J);
             j = Q.j_lo + r % Q.J + 1;
@@ -489,6 +496,17 @@ __global__ void k_woff(const uint32_t* __restrict__ keys, int64_t m, int64_t nke
         int64_t cur = i == m ? nkeys : (int64_t)keys[i];
         for (int64_t v = prev + 1; v <= cur; v++) off[v] = i;
     }
+}
+
+// last time an instance starting at t1 may use: t1 + delta, clamped to the window's end (for
+// a query whose windows are all kept, the end of t1's own window)
+__device__ __forceinline__ int64_t first_thi(const QPlan& Q, const WinDev& W, int64_t win, int64_t t1) {
+    int64_t tend = W.tend[win];
+    if (Q.wclamp) {
+        int64_t s = W.start[win];
+        tend = s + ((t1 - s) / Q.cd + 1) * Q.cd - 1;
+    }
+    return min(t1 + Q.delta, tend);
 }
 
 // window of first edge 32 b for every block b of 32 first edges: one search each,
@@ -585,7 +603,7 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
         int32_t s1, d1;
         int64_t t1;
         first_edge(G, Q.order, e1, s1, d1, t1);
-        int64_t thi = min(t1 + Q.delta, A.W.tend[wi]);
+        int64_t thi = first_thi(Q, A.W, wi, t1);
         int64_t len = 0, lo = 0, ha = 0, hh = 0;
         // a segment of a streamed graph owns the exact queries' first edges in [own_lo, own_hi)
         bool owned = t1 >= Q.own_lo && t1 < Q.own_hi;
@@ -938,7 +956,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                 int64_t e1 = A.W.lo[win] + (f - A.W.fbase[win]);
                 if (Q.full) e1 = __ldg(Q.perm + e1);
                 first_edge(G, Q.order, e1, phi[0], phi[1], t1);
-                thi = min(t1 + Q.delta, A.W.tend[win]);
+                thi = first_thi(Q, A.W, win, t1);
                 int64_t l2 = A.lo2[f];
                 if (Q.ex23) {
                     // two-node motif: item = last edge j; its middle edges number
@@ -1154,8 +1172,8 @@ __global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __r
             r.p_used = 1.0;
         } else {
             r.estimate = nsh ? zsum / nsh : 0.0;
-            r.windows = (int64_t)nsh * Q.J;
-            r.windows_kept = (int64_t)tot[A_N];
+            r.windows = (int64_t)nsh * (Q.wclamp ? Q.J_all : Q.J);
+            r.windows_kept = Q.wclamp ? (int64_t)nsh * Q.J_all : (int64_t)tot[A_N];
             r.var_hat = nsh ? vsum / nsh : 0.0;
             r.shift_var = nsh >= 2 ? wm2 / (nsh - 1) : 0.0;
             r.p_used = Q.p;
@@ -1317,7 +1335,7 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
         // (only for windows large enough to hold, on average, an edge per node: smaller
         // windows gain no locality from it and would pay for the partition)
         if (q.q_mode == TM_Q_UNIFORM && q.p >= kFullScanP && m->l >= 2 && g->m > 0 &&
-            P.J < (int64_t)1 << 31 && g->m / P.J >= (int64_t)g->n) {
+            P.J < (int64_t)1 << 31 && g->m / P.J >= (int64_t)g->n && q.p < 1.0) {
             const LevelPlan& L1 = m->lv[1];
             int ord = kOrdTime;
             if (L1.view == kOut) ord = L1.su == 0 ? kOrdOut : kOrdIn;
@@ -1329,15 +1347,41 @@ void fill_plan(QPlan& P, const tm_query& q, const tm_graph* g) {
                 P.full = 1;
             }
         }
+        // every window kept: Z_k is the sum of all window weights, so each first edge of the
+        // whole graph (in node order, as exact queries take them) is clamped to its own window
+        // and one accumulator per shift holds the sum (the integer sum is the same whatever
+        // the grouping; run_batch keeps this only when no per-window detail is asked for)
+        if (q.q_mode == TM_Q_UNIFORM && q.p == 1.0 && m->l >= 2) {
+            const LevelPlan& L1 = m->lv[1];
+            int ord = kOrdTime;
+            if (L1.view == kOut) ord = L1.su == 0 ? kOrdOut : kOrdIn;
+            else if (L1.view == kIn) ord = L1.sv == 1 ? kOrdIn : kOrdOut;
+            else if (L1.view == kPair) ord = L1.su == 0 ? kOrdOut : kOrdIn;
+            if (own_pair) ord = kOrdPair;
+            if (ord != kOrdTime) {
+                P.order = ord;
+                P.wclamp = 1;
+                P.J_all = P.J;
+                P.J = 1;
+            }
+        }
     }
+}
+
+// back to one slot per window (time-ordered first edges) for callers that need the windows
+void undo_wclamp(QPlan& P) {
+    if (!P.wclamp) return;
+    P.wclamp = 0;
+    P.J = P.J_all;
+    P.order = kOrdTime;
 }
 
 }  // namespace
 
-// the two-node tables the batch's two-node queries read: own when the middle and the last
-// edge are on the same pair, rev otherwise
 int check_query(int64_t t_max, const tm_query& q, std::string& why) { return validate_query_t(t_max, q, why); }
 
+// the two-node tables the batch's two-node queries read: own when the middle and the last
+// edge are on the same pair, rev otherwise
 template <typename TT>
 int ex_tables_for(const tm_graph* g, const std::vector<QPlan>& hp, cudaStream_t st, GraphDevT<TT>& G) {
     bool need_own = false, need_rev = false;
@@ -1377,6 +1421,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             continue;
         }
         fill_plan(hp[(size_t)i], qs[i], g);
+        if (dbg && (dbg->seg || dbg->query >= 0)) undo_wclamp(hp[(size_t)i]);   // per-window detail asked for
         if (dbg && dbg->seg) {
             // a segment of a streamed graph: the windows and first edges it owns
             QPlan& P = hp[(size_t)i];
@@ -2079,6 +2124,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
             continue;
         }
         fill_plan(P, qs[i], g);
+        undo_wclamp(P);
         P.full = 0;
         if (P.mode == TM_MODE_ESTIMATE) P.order = kOrdTime;
         P.win_base = NW;

@@ -204,8 +204,11 @@ struct QPlan {
     // exact three-edge queries of the same motif at smaller spans, counted in the same
     // enumeration (spans dsub[0..nsub) < delta; their counts go to the A_X* accumulators)
     int32_t nsub;
-    int32_t pad3;
+    // estimate with every window kept (uniform p = 1): first edges of the whole graph in node
+    // order, each clamped to its own window ((t1 - s) / cd), one accumulator slot per shift
+    int32_t wclamp;
     int64_t dsub[3];
+    int64_t J_all;       // wclamp: the windows per shift (J is then 1 slot)
     LevelPlan lv[TM_L_MAX];
 };
 constexpr int kMaxSub = 3;

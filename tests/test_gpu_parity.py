@@ -631,3 +631,28 @@ def test_exact_spans_ride_along_in_one_enumeration(tm, orc):
     for k, n in enumerate(names[:3]):
         worked = [r["first_edges"] > 0 for r in res[6 * k:6 * k + 6]]
         assert sum(worked) <= 2 and worked[0]   # groups of at most four queries
+
+
+def test_all_windows_kept_uses_whole_graph_pass(tm, orc):
+    """p = 1 keeps every window: the batch then takes every edge as a first edge in node
+    order, clamped to its own window, with one accumulator per shift.  Same estimate as the
+    per-window path of a prepared batch (bit for bit) and as the oracle."""
+    src, dst, t = synth.chung_lu_hawkes(2000, 150_000, 2.1, seed=29, horizon=4_000_000)
+    g = _graph(tm, src, dst, t)
+    qs, want = [], []
+    for n in ("cycle3", "outstar3", "pingpong", "cycle4"):
+        ms, md = synth.MOTIFS[n]
+        mo = tm.Motif(ms, md)
+        for (d, c, seed, b) in ((3600, 10, 5, 2), (600, 3, 6, 1), (86400, 30, 7, 1)):
+            qs.append(tm.estimate_query(mo, d, c, 1.0, seed, b=b))
+            want.append(orc.estimate(src, dst, t, ms, md, d, c, 1.0, seed, b=b, threads=8))
+    res = tm.run_batch(g, qs)
+    pb = tm.PreparedBatch(g, qs)
+    pb.launch()
+    prep = pb.results()
+    pb.free()
+    for q, r, p_, w in zip(qs, res, prep, want):
+        assert r["status"] == 0 and _close(r["estimate"], w), (q.delta, r["estimate"], w)
+        assert r["estimate"] == p_["estimate"] and r["count"] == p_["count"]
+        assert r["windows"] == p_["windows"] and r["windows_kept"] == p_["windows_kept"] == r["windows"]
+        assert r["var_hat"] == 0.0
