@@ -356,6 +356,69 @@ __device__ __forceinline__ void add_sub_range(Acc& a, const QPlan& Q, const TT* 
         if (i < Q.nsub) a.f[A_X0 + i] += gallop_ub(ta, lo, hi, t1 + Q.dsub[i]) - lo;
 }
 
+// the riding estimate (QPlan::nride): n instances starting at t1 and closing at t3 count
+// when they lie inside t1's window of the rider and within its span
+__device__ __forceinline__ bool ride_in(const QPlan& Q, int64_t t1, int64_t t3) {
+    int64_t s = Q.r_shift;
+    int64_t tend = s + ((t1 - s) / Q.r_cd + 1) * Q.r_cd - 1;
+    return t3 - t1 <= Q.r_delta && t3 <= tend;
+}
+
+__device__ __forceinline__ void ride_weight(const QPlan& Q, int64_t dur, unsigned long long n,
+                                            unsigned long long& lo, unsigned long long& hi) {
+    unsigned long long wi, wf;
+    if (Q.r_wtab) {
+        wi = __ldg(Q.r_wtab + 2 * dur);
+        wf = __ldg(Q.r_wtab + 2 * dur + 1);
+    } else {
+        q64_weight(Q.r_cd, dur, wi, wf);
+    }
+    lo = wf * n;
+    hi = wi * n + __umul64hi(wf, n);
+}
+
+// the rider's sums are spread over kRideSlots slots (by warp) so that their atomics do not
+// all meet at one address; the host adds the slots
+constexpr int kRideSlots = 64;
+
+__device__ __forceinline__ void ride_flush(const QPlan& Q, unsigned long long cnt, unsigned long long lo,
+                                           unsigned long long hi) {
+    if (!cnt) return;
+    unsigned long long* a =
+        Q.r_acc + 3 * (((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5) & (kRideSlots - 1));
+    atomicAdd(a, cnt);
+    unsigned long long old = atomicAdd(a + 1, lo);
+    if (old + lo < old) hi += 1;
+    if (hi) atomicAdd(a + 2, hi);
+}
+
+// cnt instances closed by the edge at t3 (out of line: rare, and it keeps the matcher's
+// registers for the common path)
+__device__ __noinline__ void ride_at(const QPlan& Q, int64_t t1, int64_t t3, unsigned long long cnt) {
+    if (!ride_in(Q, t1, t3)) return;
+    unsigned long long lo, hi;
+    ride_weight(Q, t3 - t1, cnt, lo, hi);
+    ride_flush(Q, cnt, lo, hi);
+}
+
+// one instance per closing entry of the time-sorted range [lo, hi)
+template <typename TT>
+__device__ __noinline__ void ride_range(const QPlan& Q, const TT* __restrict__ ta, int64_t lo, int64_t hi,
+                                        int64_t t1) {
+    unsigned long long cnt = 0, wl = 0, wh = 0;
+    for (int64_t j = lo; j < hi; j++) {
+        int64_t t3 = (int64_t)ta[j];
+        if (!ride_in(Q, t1, t3)) break;   // times increase: the rest are outside too
+        unsigned long long l, h;
+        ride_weight(Q, t3 - t1, 1, l, h);
+        unsigned long long x = wl + l;
+        wh += h + (x < wl ? 1ull : 0ull);
+        wl = x;
+        cnt++;
+    }
+    ride_flush(Q, cnt, wl, wh);
+}
+
 // n instances of duration dur at once: n * (wi + wf 2^-64), exactly as n single adds
 __device__ __forceinline__ void add_weight_n(Acc& a, const QPlan& Q, int64_t dur, unsigned long long n) {
     unsigned long long wi, wf;
@@ -1002,6 +1065,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                         acc.f[A_COUNT] += cnt;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
                         if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
+                        if (Q.nride) ride_at(Q, t1, t3, (unsigned long long)cnt);
                     }
                 } else if (l2 < 0) {
                     // closing-edge candidate e3 = (x, t3); count second edges in (t1, t3)
@@ -1022,6 +1086,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                             acc.f[A_COUNT] += cnt;
                             if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
                             if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
+                            if (Q.nride) ride_at(Q, t1, t3, (unsigned long long)cnt);
                         }
                     }
                 } else {
@@ -1055,6 +1120,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                         acc.f[A_COUNT] += chi - clo;
                         acc.f[A_LAST] += 1;
                         if (Q.nsub && chi > clo) add_sub_range(acc, Q, G.pair_t, clo, chi, t1);
+                        if (Q.nride && chi > clo) ride_range(Q, G.pair_t, clo, chi, t1);
                     } else {
                         deeper = ok;
                     }
@@ -1070,7 +1136,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
 }
 
 // per query: sums over its windows, per shift; Z_k and the mean (Algorithm 1)
-__global__ void k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __restrict__ res,
+__global__ void __launch_bounds__(1024) k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __restrict__ res,
                        ShiftSums* __restrict__ sums, unsigned long long* __restrict__ subc) {
     int qi = blockIdx.x;
     const QPlan& Q = plans[qi];
@@ -1443,6 +1509,14 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             P.nsub = std::min(dbg->nsub[i], (int32_t)kMaxSub);
             for (int x = 0; x < P.nsub; x++) P.dsub[x] = dbg->sub_delta[(size_t)i * kMaxSub + x];
         }
+        if (dbg && dbg->ride && hp[(size_t)i].mode == TM_MODE_EXACT && dbg->ride[(size_t)i * 4]) {
+            QPlan& P = hp[(size_t)i];
+            P.nride = 1;
+            P.r_delta = dbg->ride[(size_t)i * 4 + 1];
+            P.r_cd = dbg->ride[(size_t)i * 4 + 2];
+            P.r_shift = dbg->ride[(size_t)i * 4 + 3];
+            if (P.r_delta + 1 <= kWtabMax) wtab_bytes += a256(16 * (size_t)(P.r_delta + 1));
+        }
         hp[(size_t)i].win_base = NW;
         hp[(size_t)i].sum_base = n_sums;
         n_sums += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].b;
@@ -1465,17 +1539,22 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
                 a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1)) +
-                a256(8 * kMaxSub * (size_t)nq);
+                a256(8 * kMaxSub * (size_t)nq) + a256(8 * 3 * kRideSlots * (size_t)nq);
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
     char* p = sb;
     auto take = [&](size_t bytes) { char* r = p; p += a256(bytes); return (void*)r; };
     QPlan* dplans = (QPlan*)take(sizeof(QPlan) * (size_t)nq);
     tm_result* dres = (tm_result*)take(sizeof(tm_result) * (size_t)nq);
+    unsigned long long* dride = (unsigned long long*)take(8 * 3 * kRideSlots * (size_t)nq);
     for (int i = 0; i < nq; i++) {
         QPlan& P = hp[(size_t)i];
         if (P.l > 0 && P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) {
             P.wtab = (const uint64_t*)take(16 * (size_t)(P.delta + 1));
+        }
+        if (P.nride) {
+            P.r_acc = dride + 3 * kRideSlots * (size_t)i;
+            if (P.r_delta + 1 <= kWtabMax) P.r_wtab = (const uint64_t*)take(16 * (size_t)(P.r_delta + 1));
         }
         if (P.full) {
             P.perm = (const int32_t*)take(4 * (size_t)P.b * (size_t)g->m);
@@ -1517,12 +1596,19 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     fail(cudaMemcpyAsync(dplans, hp.data(), sizeof(QPlan) * (size_t)nq, cudaMemcpyHostToDevice, st), "plans");
     fail(cudaMemsetAsync(W.acc, 0, 8 * A_N * NWs, st), "acc");
     fail(cudaMemsetAsync(dctr, 0, 8, st), "counter");
+    fail(cudaMemsetAsync(dride, 0, 8 * 3 * kRideSlots * (size_t)nq, st), "rider sums");
     for (int i = 0; i < nq && rc == TM_OK; i++) {
         const QPlan& P = hp[(size_t)i];
         if (P.wtab) {
             int64_t n = P.delta + 1;
             unsigned gr = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
             k_wtab<<<gr, 256, 0, st>>>((uint64_t*)P.wtab, P.delta, P.cd); count_launch();
+            fail(cudaGetLastError(), "k_wtab");
+        }
+        if (P.r_wtab) {
+            int64_t n = P.r_delta + 1;
+            unsigned gr = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+            k_wtab<<<gr, 256, 0, st>>>((uint64_t*)P.r_wtab, P.r_delta, P.r_cd); count_launch();
             fail(cudaGetLastError(), "k_wtab");
         }
     }
@@ -1624,7 +1710,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     if (rc == TM_OK) {
         int ev_f0 = pe.mark(st);
-        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, dbg && dbg->sums ? dsums : nullptr,
+        k_fold<<<nq, 1024, 0, st>>>(dplans, W, dres, dbg && dbg->sums ? dsums : nullptr,
                                    dbg && dbg->sub_count ? dsubc : nullptr);
         count_launch();
         fail(cudaGetLastError(), "k_fold");
@@ -1632,6 +1718,11 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         if (ev_m1 < 0) ev_m1 = ev_f0;
     }
     if (rc == TM_OK) fail(cudaMemcpyAsync(res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
+    std::vector<unsigned long long> hride;
+    if (rc == TM_OK && dbg && dbg->ride_out) {
+        hride.resize(3 * kRideSlots * (size_t)nq);
+        fail(cudaMemcpyAsync(hride.data(), dride, 8 * hride.size(), cudaMemcpyDeviceToHost, st), "rider sums");
+    }
     if (rc == TM_OK && dbg && dbg->sub_count)
         fail(cudaMemcpyAsync(dbg->sub_count, dsubc, 8 * kMaxSub * (size_t)nq, cudaMemcpyDeviceToHost, st),
              "span counts");
@@ -1667,6 +1758,22 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     cudaError_t se = cudaStreamSynchronize(st);
     fail(se, "batch sync");
+    if (rc == TM_OK && !hride.empty()) {
+        // the riders' slots added: count, then the 128-bit weight with carries
+        for (int i = 0; i < nq; i++) {
+            unsigned long long c = 0, lo = 0, hi = 0;
+            for (int k = 0; k < kRideSlots; k++) {
+                const unsigned long long* a = &hride[(3 * kRideSlots * (size_t)i) + 3 * (size_t)k];
+                c += a[0];
+                unsigned long long x = lo + a[1];
+                hi += a[2] + (x < lo ? 1ull : 0ull);
+                lo = x;
+            }
+            dbg->ride_out[3 * (size_t)i] = c;
+            dbg->ride_out[3 * (size_t)i + 1] = lo;
+            dbg->ride_out[3 * (size_t)i + 2] = hi;
+        }
+    }
     if (pe.on && rc == TM_OK) {
         double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
         store_profile_batch(pe.ms(ev_w0, ev_w1), pe.ms(ev_l0, ev_l2), ev_l1 >= 0 ? pe.ms(ev_l1, ev_m1) : 0.0,
@@ -1747,23 +1854,56 @@ int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res
         if (!placed) groups.push_back({i});
     }
     bool any = false;
+    std::vector<int> heads;   // exact queries that do their own enumeration
     for (auto& gr : groups) {
-        if (gr.size() < 2) continue;
-        any = true;
         int L = gr[0];
         for (int i : gr)
             if (qs[i].delta > qs[L].delta) L = i;
+        heads.push_back(L);
+        if (gr.size() < 2) continue;
+        any = true;
         int k = 0;
         for (int i : gr)
             if (i != L) { lead[(size_t)i] = L; slot[(size_t)i] = k++; }
     }
+    // an estimate of the same three-edge motif that keeps every window (p = 1, one shift)
+    // rides along with an exact query of at least its span: each instance that query
+    // enumerates adds its weight when it lies inside one of the estimate's windows
+    std::vector<int> rider((size_t)nq, -1);   // exact head -> the estimate riding on it
+    std::vector<int> host((size_t)nq, -1);    // estimate -> its exact head
+    for (int i = 0; i < nq; i++) {
+        const tm_query& q = qs[i];
+        std::string why;
+        if (q.mode != TM_MODE_ESTIMATE || q.q_mode != TM_Q_UNIFORM || q.p != 1.0 || q.b != 1) continue;
+        if (!q.motif || q.motif->l != 3 || q.motif->k == 2 || q.motif->lv[2].view != kPair) continue;
+        if (validate_query(g, q, why) != TM_OK) continue;
+        for (int L : heads)
+            if (rider[(size_t)L] < 0 && qs[L].motif->k != 2 && qs[L].delta >= q.delta &&
+                same_motif(qs[L].motif, q.motif)) {
+                rider[(size_t)L] = i;
+                host[(size_t)i] = L;
+                any = true;
+                break;
+            }
+    }
     if (!any) return run_batch_typed(g, qs, nq, res, st, nullptr);
-    // the batch without the members, each leader carrying its members' spans
+    // the batch without the members and riders, each head carrying its members' spans
     std::vector<tm_query> qc;
     std::vector<int> pos((size_t)nq, -1);
     for (int i = 0; i < nq; i++)
-        if (lead[(size_t)i] < 0) { pos[(size_t)i] = (int)qc.size(); qc.push_back(qs[i]); }
+        if (lead[(size_t)i] < 0 && host[(size_t)i] < 0) { pos[(size_t)i] = (int)qc.size(); qc.push_back(qs[i]); }
     int nc = (int)qc.size();
+    std::vector<int64_t> ride((size_t)nc * 4, 0);
+    for (int i = 0; i < nq; i++) {
+        if (host[(size_t)i] < 0) continue;
+        const tm_query& q = qs[i];
+        int64_t cd = (int64_t)q.c * q.delta;
+        int64_t* r = &ride[(size_t)pos[(size_t)host[(size_t)i]] * 4];
+        r[0] = 1;
+        r[1] = q.delta;
+        r[2] = cd;
+        r[3] = -(int64_t)(draw(q.seed, 0, 0) % (uint64_t)cd);
+    }
     std::vector<int32_t> nsub((size_t)nc, 0);
     std::vector<int64_t> sd((size_t)nc * kMaxSub, 0);
     for (int i = 0; i < nq; i++) {
@@ -1773,13 +1913,37 @@ int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res
         nsub[(size_t)c] = std::max(nsub[(size_t)c], slot[(size_t)i] + 1);
     }
     std::vector<tm_result> rc_res((size_t)nc);
-    std::vector<unsigned long long> sc((size_t)nc * kMaxSub, 0);
+    std::vector<unsigned long long> sc((size_t)nc * kMaxSub, 0), ro((size_t)nc * 3, 0);
     BatchOut bo;
     bo.nsub = nsub.data();
     bo.sub_delta = sd.data();
     bo.sub_count = sc.data();
+    bo.ride = ride.data();
+    bo.ride_out = ro.data();
     int rc = run_batch_typed(g, qc.data(), nc, rc_res.data(), st, &bo);
     for (int i = 0; i < nq; i++) {
+        if (host[(size_t)i] >= 0) {
+            // the rider's result, folded as k_fold folds one shift with every window kept
+            const tm_query& q = qs[i];
+            int c = pos[(size_t)host[(size_t)i]];
+            const unsigned long long* a = &ro[(size_t)c * 3];
+            int64_t cd = (int64_t)q.c * q.delta;
+            int64_t J = 1 + (g->t_max + cd - 1) / cd;
+            tm_result r;
+            std::memset(&r, 0, sizeof(r));
+            r.status = rc_res[(size_t)c].status;
+            if (r.status == TM_OK && (a[2] >= (1ull << 63) || a[0] >= (1ull << 63))) r.status = TM_EOVERFLOW;
+            r.count = (int64_t)a[0];
+            double wd = (double)a[2] + (double)a[1] * 0x1.0p-64;
+            double zsum = 0.0;
+            zsum += wd / q.p;
+            r.estimate = zsum / 1;
+            r.windows = J;
+            r.windows_kept = J;
+            r.p_used = q.p;
+            res[i] = r;   // the enumeration, and so first_edges etc., is the exact query's
+            continue;
+        }
         if (lead[(size_t)i] < 0) {
             res[i] = rc_res[(size_t)pos[(size_t)i]];
             continue;
@@ -2261,7 +2425,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         }
     }
     if (rc == TM_OK) {
-        k_fold<<<nq, 256, 0, st>>>(dplans, W, dres, nullptr, nullptr); count_launch();
+        k_fold<<<nq, 1024, 0, st>>>(dplans, W, dres, nullptr, nullptr); count_launch();
         fail(cudaGetLastError(), "k_fold");
     }
     fail(cudaMemcpyAsync(b->h_res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");

@@ -656,3 +656,32 @@ def test_all_windows_kept_uses_whole_graph_pass(tm, orc):
         assert r["estimate"] == p_["estimate"] and r["count"] == p_["count"]
         assert r["windows"] == p_["windows"] and r["windows_kept"] == p_["windows_kept"] == r["windows"]
         assert r["var_hat"] == 0.0
+
+
+def test_estimates_keeping_every_window_ride_along_exact_queries(tm, orc):
+    """An estimate with p = 1 (one shift) of the same three-edge motif as an exact query of
+    at least its span takes its instances from that query's enumeration: results equal the
+    estimate run alone (bit for bit) and the oracle's."""
+    src, dst, t = synth.chung_lu_hawkes(2000, 150_000, 2.1, seed=33, horizon=4_000_000,
+                                        max_degree=20_000, hub_bursts=4, burst_max=300)
+    g = _graph(tm, src, dst, t)
+    qs, want = [], []
+    for n in ("cycle3", "outstar3", "pingpong"):
+        ms, md = synth.MOTIFS[n]
+        mo = tm.Motif(ms, md)
+        qs += [tm.exact_query(mo, 86400), tm.exact_query(mo, 3600)]
+        want += [("exact", orc.count_exact(src, dst, t, ms, md, 86400, threads=8)),
+                 ("exact", orc.count_exact(src, dst, t, ms, md, 3600, threads=8))]
+        for (d, c, seed) in ((86400, 30, 3), (3600, 10, 4), (600, 5, 5)):
+            qs.append(tm.estimate_query(mo, d, c, 1.0, seed))
+            want.append(("est", orc.estimate(src, dst, t, ms, md, d, c, 1.0, seed, threads=8)))
+    res = tm.run_batch(g, qs)
+    for q, r, (kind, w) in zip(qs, res, want):
+        assert r["status"] == 0
+        if kind == "exact":
+            assert r["count"] == w
+        else:
+            assert _close(r["estimate"], w), (q.delta, r["estimate"], w)
+        alone = tm.run_batch(g, [q])[0]
+        assert alone["count"] == r["count"] and alone["estimate"] == r["estimate"]
+        assert alone["windows"] == r["windows"] and alone["windows_kept"] == r["windows_kept"]
