@@ -237,14 +237,37 @@ __device__ __forceinline__ int64_t last_count_subtract(const GraphDevT<TT>& G, c
     return len - excl;
 }
 
+// Per-lane accumulator of one window.  The count and the 128-bit weight, touched on every
+// instance, live in registers; the other fields (work counters, counts of the spans that
+// ride along) live in this thread's slots of shared memory (field-major, stride = block
+// size), which keeps them out of the register budget of the matcher kernels.
+constexpr int A_NREG = 3;   // A_COUNT, A_WLO, A_WHI
 struct Acc {
     int64_t win;
-    unsigned long long f[A_N];
+    unsigned long long f[A_NREG];
+    unsigned long long* x;   // this thread's first shared-memory slot
+    int xs;                  // slot stride (threads per block)
+    __device__ __forceinline__ unsigned long long& s(int i) { return x[(i - A_NREG) * xs]; }
+    __device__ __forceinline__ unsigned long long get(int i) { return i < A_NREG ? f[i] : s(i); }
 };
+
+// dynamic shared memory of k_level2 / k_match: the staged plans, then the accumulator slots
+__host__ __device__ __forceinline__ size_t acc_smem_offset(int nq) {
+    size_t b = nq <= 64 ? sizeof(QPlan) * (size_t)nq : 0;   // kSmemPlans
+    return (b + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ void acc_init(Acc& a, unsigned char* smem, int nq) {
+    a.x = reinterpret_cast<unsigned long long*>(smem + acc_smem_offset(nq)) + threadIdx.x;
+    a.xs = blockDim.x;
+    a.win = -1;
+}
 
 __device__ __forceinline__ void acc_zero(Acc& a) {
 #pragma unroll
-    for (int i = 0; i < A_N; i++) a.f[i] = 0;
+    for (int i = 0; i < A_NREG; i++) a.f[i] = 0;
+#pragma unroll
+    for (int i = A_NREG; i < A_N; i++) a.s(i) = 0;
 }
 
 __device__ __forceinline__ void atomic_add_u128(unsigned long long* lo_hi, unsigned long long lo,
@@ -262,8 +285,10 @@ __device__ __forceinline__ void acc_flush_lane(Acc& a, unsigned long long* acc) 
     if (a.f[A_COUNT]) atomicAdd(p + A_COUNT, a.f[A_COUNT]);
     atomic_add_u128(p + A_WLO, a.f[A_WLO], a.f[A_WHI]);
 #pragma unroll
-    for (int i = A_FIRST; i < A_N; i++)
-        if (a.f[i]) atomicAdd(p + i, a.f[i]);
+    for (int i = A_FIRST; i < A_N; i++) {
+        unsigned long long v = a.s(i);
+        if (v) atomicAdd(p + i, v);
+    }
     acc_zero(a);
 }
 
@@ -281,22 +306,16 @@ __device__ __forceinline__ void acc_flush_warp(Acc& a, unsigned long long* acc) 
             hi = hi + hi2 + (s < lo ? 1ull : 0ull);
             lo = s;
         }
-        unsigned long long v[A_N];
+        unsigned long long* p = acc + w0 * A_N;
 #pragma unroll
         for (int i = 0; i < A_N; i++) {
-            v[i] = a.f[i];
             if (i == A_WLO || i == A_WHI) continue;
+            unsigned long long v = a.get(i);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(kFull, v[i], o);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(p + i, v);
         }
-        if ((threadIdx.x & 31) == 0) {
-            unsigned long long* p = acc + w0 * A_N;
-            if (v[A_COUNT]) atomicAdd(p + A_COUNT, v[A_COUNT]);
-            atomic_add_u128(p + A_WLO, lo, hi);
-#pragma unroll
-            for (int i = A_FIRST; i < A_N; i++)
-                if (v[i]) atomicAdd(p + i, v[i]);
-        }
+        if ((threadIdx.x & 31) == 0) atomic_add_u128(p + A_WLO, lo, hi);
         acc_zero(a);
     } else {
         acc_flush_lane(a, acc);
@@ -343,7 +362,7 @@ __device__ __forceinline__ void add_sub_at(Acc& a, const QPlan& Q, int64_t t1, i
                                            unsigned long long cnt) {
 #pragma unroll
     for (int i = 0; i < kMaxSub; i++)
-        if (i < Q.nsub && t3 - t1 <= Q.dsub[i]) a.f[A_X0 + i] += cnt;
+        if (i < Q.nsub && t3 - t1 <= Q.dsub[i]) a.s(A_X0 + i) += cnt;
 }
 
 // ... and the instances closed by entries (tc, t1 + dsub_i] of a time-sorted range [lo, hi)
@@ -353,7 +372,7 @@ __device__ __forceinline__ void add_sub_range(Acc& a, const QPlan& Q, const TT* 
                                               int64_t hi, int64_t t1) {
 #pragma unroll
     for (int i = 0; i < kMaxSub; i++)
-        if (i < Q.nsub) a.f[A_X0 + i] += gallop_ub(ta, lo, hi, t1 + Q.dsub[i]) - lo;
+        if (i < Q.nsub) a.s(A_X0 + i) += gallop_ub(ta, lo, hi, t1 + Q.dsub[i]) - lo;
 }
 
 // the riding estimate (QPlan::nride): n instances starting at t1 and closing at t3 count
@@ -459,6 +478,12 @@ __device__ __forceinline__ const QPlan* stage_plans(const QPlan* gplans, int nq,
 }
 
 size_t plan_smem_bytes(int nq) { return nq <= kSmemPlans ? sizeof(QPlan) * (size_t)nq : 0; }
+static_assert(kSmemPlans == 64, "acc_smem_offset assumes 64 staged plans at most");
+
+// dynamic shared memory of k_level2 / k_match: plans, then the accumulator slots
+size_t match_smem_bytes(int nq, int threads) {
+    return acc_smem_offset(nq) + (size_t)(A_N - A_NREG) * 8 * (size_t)threads;
+}
 
 // ----------------------------------------------------------------- kernels
 __global__ void k_wtab(uint64_t* __restrict__ tab, int64_t delta, int64_t cd) {
@@ -613,7 +638,7 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Acc acc;
-    acc.win = -1;
+    acc_init(acc, smem_plans, A.nq);
     acc_zero(acc);
     const int64_t F = A.d_F ? *A.d_F : A.F;
     for (int64_t base = warp * 32; base < F; base += nwarps * 32) {
@@ -670,7 +695,7 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
         int64_t len = 0, lo = 0, ha = 0, hh = 0;
         // a segment of a streamed graph owns the exact queries' first edges in [own_lo, own_hi)
         bool owned = t1 >= Q.own_lo && t1 < Q.own_hi;
-        if (owned) acc.f[A_FIRST] += 1;
+        if (owned) acc.s(A_FIRST) += 1;
         if (owned && s1 != d1) {
             if (Q.l == 1) {
                 acc.f[A_COUNT] += 1;
@@ -710,10 +735,10 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                         const int64_t* S = mid_rev == last_rev ? G.ex_own : G.ex_rev;
                         int64_t sa = __ldg(S + ha);
                         acc.f[A_COUNT] += (unsigned long long)((__ldg(S + hh) - sa) - (hh - ha) * le2);
-                        acc.f[A_LAST] += 1;
+                        acc.s(A_LAST) += 1;
                         for (int i = 0; i < Q.nsub; i++) {   // exact queries at smaller spans
                             int64_t hi = gallop_ub(G.pair_t, ha, hh, t1 + Q.dsub[i]);
-                            acc.f[A_X0 + i] += (unsigned long long)((__ldg(S + hi) - sa) - (hi - ha) * le2);
+                            acc.s(A_X0 + i) += (unsigned long long)((__ldg(S + hi) - sa) - (hi - ha) * le2);
                         }
                     } else {
                         len = hh - ha;   // items: the last edges; k_match reads ha and le2
@@ -789,11 +814,11 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                 if (Q.l == 2 && Q.mode == TM_MODE_EXACT) {
                     if (P.view == kPair) {
                         acc.f[A_COUNT] += len;
-                        acc.f[A_LAST] += 1;
+                        acc.s(A_LAST) += 1;
                         len = 0;
                     } else if (len > A.enum_threshold && P.view != kAll) {
                         acc.f[A_COUNT] += last_count_subtract(G, P, phi, len, t1, thi);
-                        acc.f[A_LAST] += 1;
+                        acc.s(A_LAST) += 1;
                         len = 0;
                     }
                 }
@@ -854,7 +879,7 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
         }
         if (D == Q.l - 1) {
             acc_switch(acc, win, A.W.acc);
-            acc.f[A_LAST] += 1;
+            acc.s(A_LAST) += 1;
             if (Q.mode == TM_MODE_EXACT) {
                 if (P.view == kPair) {
                     acc.f[A_COUNT] += len;
@@ -910,12 +935,12 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
                 int64_t c = olo + (x - ost);
                 int32_t xv = x_src ? __ldg(G.in_nbr + c) : __ldg(G.out_nbr + c);
                 int64_t tl = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
-                acc.f[A_CAND] += 1;
+                acc.s(A_CAND) += 1;
                 if (!phi_has(ophi, P.nb, xv)) {
                     int32_t mu = P.bind_u ? xv : phi_get(ophi, P.su);
                     int32_t mv = P.bind_v ? xv : phi_get(ophi, P.sv);
                     int64_t cnt = pair_count(G, mu, mv, otp, tl - 1);
-                    acc.f[A_LAST] += 1;
+                    acc.s(A_LAST) += 1;
                     if (cnt) {
                         acc.f[A_COUNT] += cnt;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, tl - ot1, (unsigned long long)cnt);
@@ -926,20 +951,20 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
                 read_cand(G, P, ophi, olo + (x - ost), s, d, tc);
                 ok = check_bind(P, ophi, s, d);
                 if (D == Q.l - 1) {
-                    acc.f[A_INST] += 1;
+                    acc.s(A_INST) += 1;
                     if (ok) {
                         acc.f[A_COUNT] += 1;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - ot1);
                     }
                 } else {
-                    acc.f[A_CAND] += 1;
+                    acc.s(A_CAND) += 1;
                     deeper = ok;
                     if constexpr (D + 2 <= LMAX) {
                         const LevelPlan L = Q.lv[Q.l - 1];
                         if (ok && D == Q.l - 2 && Q.mode == TM_MODE_EXACT && L.view == kPair && !Q.hoist) {
                             // close here: the last edge counted by range length
                             acc.f[A_COUNT] += pair_count(G, phi_get(ophi, L.su), phi_get(ophi, L.sv), tc, othi);
-                            acc.f[A_LAST] += 1;
+                            acc.s(A_LAST) += 1;
                             deeper = false;
                         }
                     }
@@ -965,7 +990,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
     int64_t W2 = *A.d_W2;
     const int64_t F = A.d_F ? *A.d_F : A.F;
     Acc acc;
-    acc.win = -1;
+    acc_init(acc, smem_plans, A.nq);
     acc_zero(acc);
     for (;;) {
         unsigned long long c0u = 0;
@@ -1030,8 +1055,8 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     int64_t t3 = __ldg(G.pair_t + j);
                     int64_t cnt = (__ldg(S + j + 1) - __ldg(S + j)) - A.hs_hi[f];
                     acc_switch(acc, win, A.W.acc);
-                    acc.f[A_CAND] += 1;
-                    acc.f[A_LAST] += 1;
+                    acc.s(A_CAND) += 1;
+                    acc.s(A_LAST) += 1;
                     if (cnt > 0) {
                         acc.f[A_COUNT] += cnt;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
@@ -1045,8 +1070,8 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     int64_t p3 = ha0 + (w - A.excl[f]);
                     int64_t t3 = __ldg(G.pair_t + p3);
                     acc_switch(acc, win, A.W.acc);
-                    acc.f[A_CAND] += 1;
-                    acc.f[A_LAST] += 1;
+                    acc.s(A_CAND) += 1;
+                    acc.s(A_LAST) += 1;
                     const TT* t1v = M1.view == kPair ? G.pair_t : M1.view == kOut ? G.out_t : G.in_t;
                     int64_t cnt = upper_bound_i64(t1v, lo1, end1, t3 - 1) - lo1;
                     if (M1.view != kPair) {
@@ -1076,12 +1101,12 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     int32_t x = x_src ? __ldg(G.in_nbr + c) : __ldg(G.out_nbr + c);
                     int64_t t3 = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
                     acc_switch(acc, win, A.W.acc);
-                    acc.f[A_CAND] += 1;
+                    acc.s(A_CAND) += 1;
                     if (x != phi[0] && x != phi[1]) {
                         int32_t mu = M1.su == 2 ? x : phi_get(phi, M1.su);
                         int32_t mv = M1.sv == 2 ? x : phi_get(phi, M1.sv);
                         int64_t cnt = pair_count(G, mu, mv, t1, t3 - 1);
-                        acc.f[A_LAST] += 1;
+                        acc.s(A_LAST) += 1;
                         if (cnt) {
                             acc.f[A_COUNT] += cnt;
                             if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
@@ -1100,13 +1125,13 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                 }
                 acc_switch(acc, win, A.W.acc);
                 if (Q.l == 2) {
-                    acc.f[A_INST] += 1;
+                    acc.s(A_INST) += 1;
                     if (ok) {
                         acc.f[A_COUNT] += 1;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - t1);
                     }
                 } else {
-                    acc.f[A_CAND] += 1;
+                    acc.s(A_CAND) += 1;
                     const LevelPlan L = Q.lv[2];
                     if (ok && Q.l == 3 && Q.mode == TM_MODE_EXACT && L.view == kPair) {
                         // close the instance here: the last edge is counted by range length
@@ -1118,7 +1143,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                             pair_range(G, phi_get(phi, L.su), phi_get(phi, L.sv), tc, thi, clo, chi);
                         }
                         acc.f[A_COUNT] += chi - clo;
-                        acc.f[A_LAST] += 1;
+                        acc.s(A_LAST) += 1;
                         if (Q.nsub && chi > clo) add_sub_range(acc, Q, G.pair_t, clo, chi, t1);
                         if (Q.nride && chi > clo) ride_range(Q, G.pair_t, clo, chi, t1);
                     } else {
@@ -1679,7 +1704,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 W.fbase, NW, F, nullptr, bwin);
             count_launch();
             ev_l0 = pe.mark(st);
-            k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
+            k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
             fail(cudaGetLastError(), "k_level2");
             ev_l2 = pe.mark(st);
             if (rc == TM_OK) rc = scan_exclusive_i64(excl, excl, F, dW2, st);
@@ -1694,13 +1719,13 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 int bps = tu.blocks_per_sm;
                 unsigned gm = (unsigned)(nsm * bps);
                 if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
-                    k_match<TT, 3, 4, 6><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-                else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                    k_match<TT, 3, 4, 6><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+                else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
                 else if (lmax <= 4 && kmax <= 4 && tu.blocks_per_sm >= 4)
-                    k_match<TT, 4, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-                else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-                else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-                else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                    k_match<TT, 4, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+                else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+                else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+                else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
                 count_launch();
                 fail(cudaGetLastError(), "k_match");
                 ev_m1 = pe.mark(st);
@@ -2182,17 +2207,17 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         A.chunk = tu.chunk_items;
         int nsm = sm_count();
         int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
-        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, len2, lo2, nullptr, nullptr);
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, len2, lo2, nullptr, nullptr);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
         rc = scan_exclusive_i64_ws(len2, excl, F, dW2, ws, kNaWsElems, st);
         if (rc != TM_OK) return rc;
         unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
-        if (P.l <= 3 && P.k <= 4) k_match<TT, 3, 4><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
-        else if (P.l <= 4 && P.k <= 4) k_match<TT, 4, 4><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
-        else if (P.l <= 4) k_match<TT, 4, TM_K_MAX><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
-        else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, tu.block_threads, plan_smem_bytes(A.nq), st>>>(A);
+        if (P.l <= 3 && P.k <= 4) k_match<TT, 3, 4><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
+        else if (P.l <= 4 && P.k <= 4) k_match<TT, 4, 4><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
+        else if (P.l <= 4) k_match<TT, 4, TM_K_MAX><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
+        else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
@@ -2400,7 +2425,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
             W.fbase, NW, Fmax, dF, bwin);
         count_launch();
-        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, plan_smem_bytes(A.nq), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
         fail(cudaGetLastError(), "k_level2");
         if (rc == TM_OK) rc = scan_exclusive_i64_dn(excl, excl, Fmax, dF, dW2, wsp2, ws2, st);
         if (rc == TM_OK) {
@@ -2413,13 +2438,13 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
             unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
             int bt = tu.block_threads;
             if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
-                k_match<TT, 3, 4, 6><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-            else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                k_match<TT, 3, 4, 6><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+            else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
             else if (lmax <= 4 && kmax <= 4 && tu.blocks_per_sm >= 4)
-                k_match<TT, 4, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-            else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-            else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
-            else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, plan_smem_bytes(A.nq), st>>>(A);
+                k_match<TT, 4, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+            else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+            else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
+            else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
             count_launch();
             fail(cudaGetLastError(), "k_match");
         }
