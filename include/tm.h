@@ -306,6 +306,9 @@ typedef struct {
     int64_t match_items;    /* second-edge candidates the matcher processed */
     int64_t first_edges;    /* first edges the batch scanned */
     int64_t launches;       /* kernel launches since load */
+    double sizing_ms;       /* last batch: first-edge count to the host, per-edge scratch,
+                               window-of-block index (between windows_ms and level2_ms) */
+    double scan_ms;         /* last batch: scan of the range lengths, chunk index */
 } tm_profile;
 int tm_profile_enable(int32_t on);
 /* Return device memory that freed graphs and batch scratch left in the library's

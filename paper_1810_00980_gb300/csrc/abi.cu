@@ -34,8 +34,11 @@ bool profiling() { return g_prof_on.load(std::memory_order_relaxed); }
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void store_profile_batch(double windows_ms, double level2_ms, double match_ms, double fold_ms,
-                         double batch_ms, int64_t match_items, int64_t first_edges) {
+                         double batch_ms, int64_t match_items, int64_t first_edges, double sizing_ms,
+                         double scan_ms) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.sizing_ms = sizing_ms;
+    g_prof.scan_ms = scan_ms;
     g_prof.windows_ms = windows_ms;
     g_prof.level2_ms = level2_ms;
     g_prof.match_ms = match_ms;

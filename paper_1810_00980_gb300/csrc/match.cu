@@ -629,7 +629,7 @@ __global__ void k_chunkf(const int64_t* __restrict__ excl, int64_t Fh, const int
 // one warp-uniform grid-stride loop over first edges f
 template <typename TT>
 __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __restrict__ fwin,
-                                                int64_t* __restrict__ len2, int64_t* __restrict__ lo2,
+                                                int32_t* __restrict__ len2, int64_t* __restrict__ lo2,
                                                 int64_t* __restrict__ hs_a, int64_t* __restrict__ hs_hi) {
     const GraphDevT<TT>& G = A.G;
     extern __shared__ __align__(16) unsigned char smem_plans[];
@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
             }
         }
         fwin[f] = (int32_t)wi;
-        len2[f] = len;
+        len2[f] = (int32_t)len;   // a range inside one view: below 2^31
         lo2[f] = lo;
         if (hs_a) {
             hs_a[f] = ha;
@@ -1679,14 +1679,15 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         size_t Fs = (size_t)F;
         size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
         fail(cudaMallocAsync((void**)&fb, a256(4 * Fs) + (any_hoist ? 5 : 3) * a256(8 * Fs) + a256(4 * nbw) +
-                                              a256(8 * ncf), st),
+                                              a256(8 * ncf) + a256(4 * Fs), st),
              "per-edge scratch");
         if (rc == TM_OK) {
             char* q2 = fb;
             auto take2 = [&](size_t bytes) { char* r = q2; q2 += a256(bytes); return (void*)r; };
             int32_t* fwin = (int32_t*)take2(4 * Fs);
             int64_t* lo2 = (int64_t*)take2(8 * Fs);
-            int64_t* excl = (int64_t*)take2(8 * Fs);   // range lengths, then their exclusive scan in place
+            int64_t* excl = (int64_t*)take2(8 * Fs);   // exclusive scan of the range lengths
+            int32_t* len32 = (int32_t*)take2(4 * Fs);
             int64_t* hs_a = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             int64_t* hs_hi = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             int32_t* bwin = (int32_t*)take2(4 * nbw);
@@ -1704,10 +1705,10 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 W.fbase, NW, F, nullptr, bwin);
             count_launch();
             ev_l0 = pe.mark(st);
-            k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
+            k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, len32, lo2, hs_a, hs_hi); count_launch();
             fail(cudaGetLastError(), "k_level2");
             ev_l2 = pe.mark(st);
-            if (rc == TM_OK) rc = scan_exclusive_i64(excl, excl, F, dW2, st);
+            if (rc == TM_OK) rc = scan_lengths(len32, excl, F, nullptr, dW2, nullptr, 0, st);
             if (rc == TM_OK) {
                 k_chunkf<<<(unsigned)std::min<int64_t>(((int64_t)ncf + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
                     excl, F, nullptr, dW2, A.chunk, (int64_t)ncf, cf);
@@ -1802,7 +1803,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     if (pe.on && rc == TM_OK) {
         double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
         store_profile_batch(pe.ms(ev_w0, ev_w1), pe.ms(ev_l0, ev_l2), ev_l1 >= 0 ? pe.ms(ev_l1, ev_m1) : 0.0,
-                            pe.ms(ev_m1 >= 0 && ev_l1 >= 0 ? ev_m1 : ev_f1, ev_f1), wall, hW2, F);
+                            pe.ms(ev_m1 >= 0 && ev_l1 >= 0 ? ev_m1 : ev_f1, ev_f1), wall, hW2, F,
+                            ev_l0 >= 0 ? pe.ms(ev_w1, ev_l0) : 0.0, ev_l1 >= 0 ? pe.ms(ev_l2, ev_l1) : 0.0);
     }
     if (fb) cudaFreeAsync(fb, st);
     cudaFreeAsync(sb, st);
@@ -2207,11 +2209,13 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         A.chunk = tu.chunk_items;
         int nsm = sm_count();
         int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
-        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, len2, lo2, nullptr, nullptr);
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, (int32_t*)len2, lo2, nullptr, nullptr);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
-        rc = scan_exclusive_i64_ws(len2, excl, F, dW2, ws, kNaWsElems, st);
+        // the 32-bit lengths fill the first half of their 8-byte-per-edge region; the scan's
+        // workspace takes the second half
+        rc = scan_lengths((const int32_t*)len2, excl, F, nullptr, dW2, len2 + kNaMaxEdges / 2, kNaMaxEdges / 2, st);
         if (rc != TM_OK) return rc;
         unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
         if (P.l <= 3 && P.k <= 4) k_match<TT, 3, 4><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
@@ -2330,7 +2334,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2) +
-                a256(4 * (Fs / 32 + 1)) + a256(8 * (Fs / 4 + 2));
+                a256(4 * (Fs / 32 + 1)) + a256(8 * (Fs / 4 + 2)) + a256(4 * Fs);
     cudaError_t e = cudaMalloc(&b->scratch, sz);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_res, sizeof(tm_result) * (size_t)nq);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -2369,6 +2373,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     int32_t* fwin = (int32_t*)take(4 * Fs);
     int64_t* lo2 = (int64_t*)take(8 * Fs);
     int64_t* excl = (int64_t*)take(8 * Fs);
+    int32_t* len32 = (int32_t*)take(4 * Fs);
     int64_t* hs_a = any_hoist ? (int64_t*)take(8 * Fs) : nullptr;
     int64_t* hs_hi = any_hoist ? (int64_t*)take(8 * Fs) : nullptr;
     int64_t* wsp1 = (int64_t*)take(8 * (size_t)ws1);
@@ -2425,9 +2430,9 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
             W.fbase, NW, Fmax, dF, bwin);
         count_launch();
-        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, excl, lo2, hs_a, hs_hi); count_launch();
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, len32, lo2, hs_a, hs_hi); count_launch();
         fail(cudaGetLastError(), "k_level2");
-        if (rc == TM_OK) rc = scan_exclusive_i64_dn(excl, excl, Fmax, dF, dW2, wsp2, ws2, st);
+        if (rc == TM_OK) rc = scan_lengths(len32, excl, Fmax, dF, dW2, wsp2, ws2, st);
         if (rc == TM_OK) {
             k_chunkf<<<(unsigned)std::min<int64_t>(((int64_t)ncf + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
                 excl, Fmax, dF, dW2, A.chunk, (int64_t)ncf, cf);

@@ -69,6 +69,60 @@ __global__ void k_scan_tiles(const int64_t* in, int64_t* out, int64_t n, int64_t
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
+// 32-bit lengths -> 64-bit exclusive offsets, reduce-then-scan (each length read twice, each
+// offset written once): per-tile sums first (tiles at or past the count, read on the device
+// when d_n is given, sum to 0) ...
+__global__ void k_len_reduce(const int32_t* __restrict__ in, int64_t n_max, const int64_t* __restrict__ d_n,
+                             int64_t* __restrict__ sums) {
+    __shared__ int64_t smem[33];
+    int64_t n = d_n ? min(*d_n, n_max) : n_max;
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t loc = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        int64_t idx = base + i;
+        if (idx < n) loc += in[idx];
+    }
+    int64_t total;
+    block_excl_scan(loc, smem, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// ... then each tile's exclusive scan plus the tile's offset; the tile passes through shared
+// memory so that both the 32-bit loads and the 64-bit stores are coalesced
+__global__ void k_len_scan(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n_max,
+                           const int64_t* __restrict__ d_n, const int64_t* __restrict__ offs) {
+    __shared__ int64_t smem[33];
+    __shared__ int64_t tile[kScanTile + kScanTile / 16];   // one pad word per 16: no bank conflicts
+    int64_t n = d_n ? min(*d_n, n_max) : n_max;
+    int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+    if (t0 >= n) return;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        int64_t idx = t0 + i;
+        tile[i + (i >> 4)] = idx < n ? (int64_t)in[idx] : 0;
+    }
+    __syncthreads();
+    int b = threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        v[i] = tile[b + i + ((b + i) >> 4)];
+        loc += v[i];
+    }
+    int64_t total;
+    int64_t run = block_excl_scan(loc, smem, &total) + offs[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        tile[b + i + ((b + i) >> 4)] = run;
+        run += v[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        int64_t idx = t0 + i;
+        if (idx < n) out[idx] = tile[i + (i >> 4)];
+    }
+}
+
 __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ offs) {
     int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t add = offs[blockIdx.x];
@@ -422,6 +476,41 @@ int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d
     k_scan_add<<<(unsigned)ntiles, kScanThreads, 0, st>>>(out, n, soffs); count_launch();
     TM_CUDA(cudaGetLastError());
     return TM_OK;
+}
+
+int scan_lengths(const int32_t* in, int64_t* out, int64_t n_max, const int64_t* d_n, int64_t* d_total,
+                 int64_t* ws, int64_t ws_elems, cudaStream_t st) {
+    if (n_max <= 0) {
+        if (d_total) {
+            k_set_i64<<<1, 1, 0, st>>>(d_total, 0); count_launch();
+            TM_CUDA(cudaGetLastError());
+        }
+        return TM_OK;
+    }
+    int64_t ntiles = (n_max + kScanTile - 1) / kScanTile;
+    int64_t need = 2 * ntiles + 2 * ((ntiles + kScanTile - 1) / kScanTile) + 2;
+    int64_t* own = nullptr;
+    if (!ws) {
+        TM_CUDA(cudaMallocAsync((void**)&own, sizeof(int64_t) * (size_t)need, st));
+        ws = own;
+        ws_elems = need;
+    }
+    int rc = TM_OK;
+    if (ws_elems < need || ntiles > (int64_t)kScanTile * kScanTile) rc = TM_EINVAL;
+    if (rc == TM_OK) {
+        int64_t* sums = ws;
+        int64_t* soffs = ws + ntiles;
+        k_len_reduce<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n_max, d_n, sums); count_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        if (rc == TM_OK) rc = scan_exclusive_i64_ws(sums, soffs, ntiles, d_total, ws + 2 * ntiles, need - 2 * ntiles, st);
+        if (rc == TM_OK) {
+            k_len_scan<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, n_max, d_n, soffs); count_launch();
+            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        }
+    }
+    if (own) cudaFreeAsync(own, st);
+    if (rc != TM_OK) set_error("length scan failed");
+    return rc;
 }
 
 int64_t scan_dn_ws_elems(int64_t n_max) {

@@ -282,6 +282,10 @@ int scan_exclusive_i64_ws(const int64_t* in, int64_t* out, int64_t n, int64_t* d
 // exclusive scan of the first *d_n (<= n_max) elements, the count read on the
 // device; workspace of scan_dn_ws_elems(n_max) int64 (no allocation, capturable)
 int64_t scan_dn_ws_elems(int64_t n_max);
+// exclusive scan of 32-bit lengths into 64-bit offsets (the first *d_n, or n_max when d_n is
+// null); workspace scan_dn_ws_elems(n_max), or null to allocate it on the stream
+int scan_lengths(const int32_t* in, int64_t* out, int64_t n_max, const int64_t* d_n, int64_t* d_total,
+                 int64_t* ws, int64_t ws_elems, cudaStream_t st);
 int scan_exclusive_i64_dn(const int64_t* in, int64_t* out, int64_t n_max, const int64_t* d_n,
                           int64_t* d_total, int64_t* ws, int64_t ws_elems, cudaStream_t st);
 
@@ -300,7 +304,8 @@ int pool_trim();
 // profiling (abi.cu): phase events of the last batch / graph build, launch counter
 bool profiling();
 void store_profile_batch(double windows_ms, double level2_ms, double match_ms, double fold_ms,
-                         double batch_ms, int64_t match_items, int64_t first_edges);
+                         double batch_ms, int64_t match_items, int64_t first_edges, double sizing_ms,
+                         double scan_ms);
 void store_profile_graph(double graph_ms);
 void count_launch(int n = 1);
 

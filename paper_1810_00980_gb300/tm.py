@@ -64,7 +64,7 @@ class ServeCfg(ctypes.Structure):
 class ProfileC(ctypes.Structure):
     _fields_ = [("graph_ms", _c_dbl), ("windows_ms", _c_dbl), ("level2_ms", _c_dbl), ("match_ms", _c_dbl),
                 ("fold_ms", _c_dbl), ("batch_ms", _c_dbl), ("match_items", _c_i64), ("first_edges", _c_i64),
-                ("launches", _c_i64)]
+                ("launches", _c_i64), ("sizing_ms", _c_dbl), ("scan_ms", _c_dbl)]
 
 
 class TmError(RuntimeError):
