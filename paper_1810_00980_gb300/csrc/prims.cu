@@ -48,23 +48,35 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* smem, int
 // Each block scans one tile (exclusive), writes the tile total to sums[tile].
 // (in may equal out: every thread reads its items before any thread writes)
 __global__ void k_scan_tiles(const int64_t* in, int64_t* out, int64_t n, int64_t* __restrict__ sums) {
+    // the tile passes through shared memory (padded: no bank conflicts) so that loads and
+    // stores are coalesced
     __shared__ int64_t smem[33];
-    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    __shared__ int64_t tile[kScanTile + kScanTile / 16];
+    int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        int64_t idx = t0 + i;
+        tile[i + (i >> 4)] = idx < n ? in[idx] : 0;
+    }
+    __syncthreads();
+    int b = threadIdx.x * kScanItems;
     int64_t v[kScanItems];
     int64_t loc = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
-        int64_t idx = base + i;
-        v[i] = idx < n ? in[idx] : 0;
+        v[i] = tile[b + i + ((b + i) >> 4)];
         loc += v[i];
     }
     int64_t total;
     int64_t run = block_excl_scan(loc, smem, &total);
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
-        int64_t idx = base + i;
-        if (idx < n) out[idx] = run;
+        tile[b + i + ((b + i) >> 4)] = run;
         run += v[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        int64_t idx = t0 + i;
+        if (idx < n) out[idx] = tile[i + (i >> 4)];
     }
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
@@ -246,12 +258,6 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int s
     for (int i = threadIdx.x; i < nd; i += blockDim.x) hist[(int64_t)i * ntiles + blockIdx.x] = h[i];
 }
 
-__global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        b[i] = a[i];
-}
-
 // Stable scatter of one tile: warp w owns items [w*512, w*512+512) of the
 // tile, taken 32 at a time in index order; ranks among equal digits come from
 // __match_any_sync and per-warp running counters, then warps are offset by
@@ -401,8 +407,7 @@ int radix_sort_t(uint32_t* keys, V* vals, uint32_t* keys_tmp, V* vals_tmp, int64
         int width = (shift + db > bits) ? bits - shift : db;
         k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ka, n, shift, width, hist, ntiles); count_launch();
         int64_t nhp = ((int64_t)1 << width) * ntiles;
-        k_i32_to_i64<<<(unsigned)((nhp + 255) / 256 < 4096 ? (nhp + 255) / 256 : 4096), 256, 0, st>>>(hist, hist64, nhp); count_launch();
-        rc = scan_exclusive_i64(hist64, offs, nhp, nullptr, st);
+        rc = scan_lengths(hist, offs, nhp, nullptr, nullptr, nh >= 8 ? hist64 : nullptr, nh, st);
         if (rc != TM_OK) break;
         k_radix_scatter<V><<<(unsigned)ntiles, kSortThreads, sort_smem_bytes<V>(width), st>>>(
             ka, va, kb, vb, n, shift, width, offs, ntiles);
@@ -496,7 +501,7 @@ int scan_lengths(const int32_t* in, int64_t* out, int64_t n_max, const int64_t* 
         ws_elems = need;
     }
     int rc = TM_OK;
-    if (ws_elems < need || ntiles > (int64_t)kScanTile * kScanTile) rc = TM_EINVAL;
+    if (ws_elems < need || ntiles > (int64_t)kScanTile * kScanTile) rc = TM_EINVAL;   // caller's workspace too small
     if (rc == TM_OK) {
         int64_t* sums = ws;
         int64_t* soffs = ws + ntiles;
