@@ -375,67 +375,82 @@ __device__ __forceinline__ void add_sub_range(Acc& a, const QPlan& Q, const TT* 
         if (i < Q.nsub) a.s(A_X0 + i) += gallop_ub(ta, lo, hi, t1 + Q.dsub[i]) - lo;
 }
 
-// the riding estimate (QPlan::nride): n instances starting at t1 and closing at t3 count
-// when they lie inside t1's window of the rider and within its span
-__device__ __forceinline__ bool ride_in(const QPlan& Q, int64_t t1, int64_t t3) {
-    int64_t s = Q.r_shift;
-    int64_t tend = s + ((t1 - s) / Q.r_cd + 1) * Q.r_cd - 1;
-    return t3 - t1 <= Q.r_delta && t3 <= tend;
+// ---- estimates riding along with an exact query (QPlan::nride / riding).  An instance with
+// first edge at t1 and last edge at t3 counts for rider R's shift k when the window of t1 is
+// kept and holds t3, and t3 - t1 <= R.delta; it adds R's Q64 weight to that window's sums.
+// Out of line: rare next to the enumeration, and it keeps the matcher's registers.
+__device__ __forceinline__ void ride_window(const QPlan& R, int k, int64_t t1, int64_t& w, int64_t& thi) {
+    int64_t s = -(int64_t)(draw(R.seed, (uint64_t)k, 0) % (uint64_t)R.cd) - R.t_off;
+    int64_t j = (t1 - s) / R.cd;   // 0-based window of t1
+    w = R.win_base + (int64_t)k * R.J + j;
+    thi = min(t1 + R.delta, s + (j + 1) * R.cd - 1);
 }
 
-__device__ __forceinline__ void ride_weight(const QPlan& Q, int64_t dur, unsigned long long n,
+__device__ __forceinline__ void ride_add(unsigned long long* acc, int64_t w, unsigned long long cnt,
+                                         unsigned long long lo, unsigned long long hi) {
+    if (!cnt) return;
+    unsigned long long* p = acc + w * A_N;
+    atomicAdd(p + A_COUNT, cnt);
+    atomic_add_u128(p + A_WLO, lo, hi);
+}
+
+__device__ __forceinline__ void ride_weight(const QPlan& R, int64_t dur, unsigned long long n,
                                             unsigned long long& lo, unsigned long long& hi) {
     unsigned long long wi, wf;
-    if (Q.r_wtab) {
-        wi = __ldg(Q.r_wtab + 2 * dur);
-        wf = __ldg(Q.r_wtab + 2 * dur + 1);
+    if (R.wtab) {
+        wi = __ldg(R.wtab + 2 * dur);
+        wf = __ldg(R.wtab + 2 * dur + 1);
     } else {
-        q64_weight(Q.r_cd, dur, wi, wf);
+        q64_weight(R.cd, dur, wi, wf);
     }
     lo = wf * n;
     hi = wi * n + __umul64hi(wf, n);
 }
 
-// the rider's sums are spread over kRideSlots slots (by warp) so that their atomics do not
-// all meet at one address; the host adds the slots
-constexpr int kRideSlots = 64;
-
-__device__ __forceinline__ void ride_flush(const QPlan& Q, unsigned long long cnt, unsigned long long lo,
-                                           unsigned long long hi) {
-    if (!cnt) return;
-    unsigned long long* a =
-        Q.r_acc + 3 * (((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5) & (kRideSlots - 1));
-    atomicAdd(a, cnt);
-    unsigned long long old = atomicAdd(a + 1, lo);
-    if (old + lo < old) hi += 1;
-    if (hi) atomicAdd(a + 2, hi);
-}
-
-// cnt instances closed by the edge at t3 (out of line: rare, and it keeps the matcher's
-// registers for the common path)
-__device__ __noinline__ void ride_at(const QPlan& Q, int64_t t1, int64_t t3, unsigned long long cnt) {
-    if (!ride_in(Q, t1, t3)) return;
-    unsigned long long lo, hi;
-    ride_weight(Q, t3 - t1, cnt, lo, hi);
-    ride_flush(Q, cnt, lo, hi);
-}
-
-// one instance per closing entry of the time-sorted range [lo, hi)
-template <typename TT>
-__device__ __noinline__ void ride_range(const QPlan& Q, const TT* __restrict__ ta, int64_t lo, int64_t hi,
-                                        int64_t t1) {
-    unsigned long long cnt = 0, wl = 0, wh = 0;
-    for (int64_t j = lo; j < hi; j++) {
-        int64_t t3 = (int64_t)ta[j];
-        if (!ride_in(Q, t1, t3)) break;   // times increase: the rest are outside too
-        unsigned long long l, h;
-        ride_weight(Q, t3 - t1, 1, l, h);
-        unsigned long long x = wl + l;
-        wh += h + (x < wl ? 1ull : 0ull);
-        wl = x;
-        cnt++;
+// cnt instances closed by the edge at t3
+__device__ __noinline__ void ride_at(const QPlan* __restrict__ PL, const QPlan& Q, const int32_t* __restrict__ kept,
+                                     unsigned long long* acc, int64_t t1, int64_t t3, unsigned long long cnt) {
+    for (int r = 0; r < Q.nride; r++) {
+        const QPlan& R = PL[Q.ride_q[r]];
+        if (t3 - t1 > R.delta) continue;
+        for (int k = 0; k < R.b; k++) {
+            int64_t w, thi;
+            ride_window(R, k, t1, w, thi);
+            if (t3 > thi || !kept[w]) continue;
+            unsigned long long lo, hi;
+            ride_weight(R, t3 - t1, cnt, lo, hi);
+            ride_add(acc, w, cnt, lo, hi);
+        }
     }
-    ride_flush(Q, cnt, wl, wh);
+}
+
+// one instance per closing entry of the time-sorted range [lo, hi) (entries after tc)
+template <typename TT>
+__device__ __noinline__ void ride_range(const QPlan* __restrict__ PL, const QPlan& Q,
+                                        const int32_t* __restrict__ kept, unsigned long long* acc,
+                                        const TT* __restrict__ ta, int64_t clo, int64_t chi, int64_t t1,
+                                        int64_t tc) {
+    for (int r = 0; r < Q.nride; r++) {
+        const QPlan& R = PL[Q.ride_q[r]];
+        if (t1 + R.delta <= tc) continue;   // no closing edge after tc fits the span
+        for (int k = 0; k < R.b; k++) {
+            int64_t w, thi;
+            ride_window(R, k, t1, w, thi);
+            if (thi <= tc || !kept[w]) continue;
+            unsigned long long cnt = 0, wl = 0, wh = 0;
+            for (int64_t x = clo; x < chi; x++) {
+                int64_t t3 = (int64_t)ta[x];
+                if (t3 > thi) break;   // times increase
+                unsigned long long l, h;
+                ride_weight(R, t3 - t1, 1, l, h);
+                unsigned long long y = wl + l;
+                wh += h + (y < wl ? 1ull : 0ull);
+                wl = y;
+                cnt++;
+            }
+            ride_add(acc, w, cnt, wl, wh);
+        }
+    }
 }
 
 // n instances of duration dur at once: n * (wi + wf 2^-64), exactly as n single adds
@@ -562,7 +577,7 @@ __global__ void k_windows(GraphDevT<TT> G, const QPlan* __restrict__ plans, int 
         }
         W.lo[w] = lo; W.hi[w] = hi; W.tend[w] = tend; W.start[w] = start; W.j[w] = j;
         W.q[w] = lo_q; W.k[w] = k; W.kept[w] = kept; W.qj[w] = qj;
-        W.nfirst[w] = kept ? hi - lo : 0;
+        W.nfirst[w] = (kept && !Q.riding) ? hi - lo : 0;   // riders take no first edges
     }
 }
 
@@ -1090,7 +1105,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                         acc.f[A_COUNT] += cnt;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
                         if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
-                        if (Q.nride) ride_at(Q, t1, t3, (unsigned long long)cnt);
+                        if (Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
                     }
                 } else if (l2 < 0) {
                     // closing-edge candidate e3 = (x, t3); count second edges in (t1, t3)
@@ -1111,7 +1126,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                             acc.f[A_COUNT] += cnt;
                             if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
                             if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
-                            if (Q.nride) ride_at(Q, t1, t3, (unsigned long long)cnt);
+                            if (Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
                         }
                     }
                 } else {
@@ -1145,7 +1160,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                         acc.f[A_COUNT] += chi - clo;
                         acc.s(A_LAST) += 1;
                         if (Q.nsub && chi > clo) add_sub_range(acc, Q, G.pair_t, clo, chi, t1);
-                        if (Q.nride && chi > clo) ride_range(Q, G.pair_t, clo, chi, t1);
+                        if (Q.nride && chi > clo) ride_range(PL, Q, A.W.kept, A.W.acc, G.pair_t, clo, chi, t1, tc);
                     } else {
                         deeper = ok;
                     }
@@ -1534,13 +1549,17 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             P.nsub = std::min(dbg->nsub[i], (int32_t)kMaxSub);
             for (int x = 0; x < P.nsub; x++) P.dsub[x] = dbg->sub_delta[(size_t)i * kMaxSub + x];
         }
-        if (dbg && dbg->ride && hp[(size_t)i].mode == TM_MODE_EXACT && dbg->ride[(size_t)i * 4]) {
+        if (dbg && dbg->ride_q && hp[(size_t)i].mode == TM_MODE_EXACT) {
             QPlan& P = hp[(size_t)i];
-            P.nride = 1;
-            P.r_delta = dbg->ride[(size_t)i * 4 + 1];
-            P.r_cd = dbg->ride[(size_t)i * 4 + 2];
-            P.r_shift = dbg->ride[(size_t)i * 4 + 3];
-            if (P.r_delta + 1 <= kWtabMax) wtab_bytes += a256(16 * (size_t)(P.r_delta + 1));
+            for (int x = 0; x < kMaxRide; x++)
+                if (dbg->ride_q[(size_t)i * kMaxRide + x] >= 0) P.ride_q[P.nride++] = dbg->ride_q[(size_t)i * kMaxRide + x];
+        }
+        if (dbg && dbg->riding && dbg->riding[i] && hp[(size_t)i].mode == TM_MODE_ESTIMATE) {
+            QPlan& P = hp[(size_t)i];
+            undo_wclamp(P);   // its instances arrive per window
+            P.riding = 1;
+            P.full = 0;
+            P.order = kOrdTime;
         }
         hp[(size_t)i].win_base = NW;
         hp[(size_t)i].sum_base = n_sums;
@@ -1564,22 +1583,17 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
                 a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1)) +
-                a256(8 * kMaxSub * (size_t)nq) + a256(8 * 3 * kRideSlots * (size_t)nq);
+                a256(8 * kMaxSub * (size_t)nq);
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
     char* p = sb;
     auto take = [&](size_t bytes) { char* r = p; p += a256(bytes); return (void*)r; };
     QPlan* dplans = (QPlan*)take(sizeof(QPlan) * (size_t)nq);
     tm_result* dres = (tm_result*)take(sizeof(tm_result) * (size_t)nq);
-    unsigned long long* dride = (unsigned long long*)take(8 * 3 * kRideSlots * (size_t)nq);
     for (int i = 0; i < nq; i++) {
         QPlan& P = hp[(size_t)i];
         if (P.l > 0 && P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) {
             P.wtab = (const uint64_t*)take(16 * (size_t)(P.delta + 1));
-        }
-        if (P.nride) {
-            P.r_acc = dride + 3 * kRideSlots * (size_t)i;
-            if (P.r_delta + 1 <= kWtabMax) P.r_wtab = (const uint64_t*)take(16 * (size_t)(P.r_delta + 1));
         }
         if (P.full) {
             P.perm = (const int32_t*)take(4 * (size_t)P.b * (size_t)g->m);
@@ -1621,19 +1635,12 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     fail(cudaMemcpyAsync(dplans, hp.data(), sizeof(QPlan) * (size_t)nq, cudaMemcpyHostToDevice, st), "plans");
     fail(cudaMemsetAsync(W.acc, 0, 8 * A_N * NWs, st), "acc");
     fail(cudaMemsetAsync(dctr, 0, 8, st), "counter");
-    fail(cudaMemsetAsync(dride, 0, 8 * 3 * kRideSlots * (size_t)nq, st), "rider sums");
     for (int i = 0; i < nq && rc == TM_OK; i++) {
         const QPlan& P = hp[(size_t)i];
         if (P.wtab) {
             int64_t n = P.delta + 1;
             unsigned gr = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
             k_wtab<<<gr, 256, 0, st>>>((uint64_t*)P.wtab, P.delta, P.cd); count_launch();
-            fail(cudaGetLastError(), "k_wtab");
-        }
-        if (P.r_wtab) {
-            int64_t n = P.r_delta + 1;
-            unsigned gr = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
-            k_wtab<<<gr, 256, 0, st>>>((uint64_t*)P.r_wtab, P.r_delta, P.r_cd); count_launch();
             fail(cudaGetLastError(), "k_wtab");
         }
     }
@@ -1744,11 +1751,6 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         if (ev_m1 < 0) ev_m1 = ev_f0;
     }
     if (rc == TM_OK) fail(cudaMemcpyAsync(res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
-    std::vector<unsigned long long> hride;
-    if (rc == TM_OK && dbg && dbg->ride_out) {
-        hride.resize(3 * kRideSlots * (size_t)nq);
-        fail(cudaMemcpyAsync(hride.data(), dride, 8 * hride.size(), cudaMemcpyDeviceToHost, st), "rider sums");
-    }
     if (rc == TM_OK && dbg && dbg->sub_count)
         fail(cudaMemcpyAsync(dbg->sub_count, dsubc, 8 * kMaxSub * (size_t)nq, cudaMemcpyDeviceToHost, st),
              "span counts");
@@ -1784,22 +1786,6 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     cudaError_t se = cudaStreamSynchronize(st);
     fail(se, "batch sync");
-    if (rc == TM_OK && !hride.empty()) {
-        // the riders' slots added: count, then the 128-bit weight with carries
-        for (int i = 0; i < nq; i++) {
-            unsigned long long c = 0, lo = 0, hi = 0;
-            for (int k = 0; k < kRideSlots; k++) {
-                const unsigned long long* a = &hride[(3 * kRideSlots * (size_t)i) + 3 * (size_t)k];
-                c += a[0];
-                unsigned long long x = lo + a[1];
-                hi += a[2] + (x < lo ? 1ull : 0ull);
-                lo = x;
-            }
-            dbg->ride_out[3 * (size_t)i] = c;
-            dbg->ride_out[3 * (size_t)i + 1] = lo;
-            dbg->ride_out[3 * (size_t)i + 2] = hi;
-        }
-    }
     if (pe.on && rc == TM_OK) {
         double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
         store_profile_batch(pe.ms(ev_w0, ev_w1), pe.ms(ev_l0, ev_l2), ev_l1 >= 0 ? pe.ms(ev_l1, ev_m1) : 0.0,
@@ -1893,43 +1879,40 @@ int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res
         for (int i : gr)
             if (i != L) { lead[(size_t)i] = L; slot[(size_t)i] = k++; }
     }
-    // an estimate of the same three-edge motif that keeps every window (p = 1, one shift)
-    // rides along with an exact query of at least its span: each instance that query
-    // enumerates adds its weight when it lies inside one of the estimate's windows
-    std::vector<int> rider((size_t)nq, -1);   // exact head -> the estimate riding on it
+    // estimates of the same three-edge motif with a span no larger than an exact query's ride
+    // along with it: each instance that query enumerates also adds its weight to the window of
+    // an estimate when it lies inside one of its kept windows and within its span, so the
+    // estimate needs no enumeration of its own (its windows and fold stay its own)
     std::vector<int> host((size_t)nq, -1);    // estimate -> its exact head
+    std::vector<int> nrid((size_t)nq, 0);
     for (int i = 0; i < nq; i++) {
         const tm_query& q = qs[i];
         std::string why;
-        if (q.mode != TM_MODE_ESTIMATE || q.q_mode != TM_Q_UNIFORM || q.p != 1.0 || q.b != 1) continue;
+        if (q.mode != TM_MODE_ESTIMATE || (q.q_mode != TM_Q_UNIFORM && q.q_mode != TM_Q_EDGES)) continue;
         if (!q.motif || q.motif->l != 3 || q.motif->k == 2 || q.motif->lv[2].view != kPair) continue;
         if (validate_query(g, q, why) != TM_OK) continue;
         for (int L : heads)
-            if (rider[(size_t)L] < 0 && qs[L].motif->k != 2 && qs[L].delta >= q.delta &&
+            if (nrid[(size_t)L] < kMaxRide && qs[L].motif->k != 2 && qs[L].delta >= q.delta &&
                 same_motif(qs[L].motif, q.motif)) {
-                rider[(size_t)L] = i;
                 host[(size_t)i] = L;
+                nrid[(size_t)L]++;
                 any = true;
                 break;
             }
     }
     if (!any) return run_batch_typed(g, qs, nq, res, st, nullptr);
-    // the batch without the members and riders, each head carrying its members' spans
+    // the batch without the span members, each head carrying its members' spans and riders
     std::vector<tm_query> qc;
     std::vector<int> pos((size_t)nq, -1);
     for (int i = 0; i < nq; i++)
-        if (lead[(size_t)i] < 0 && host[(size_t)i] < 0) { pos[(size_t)i] = (int)qc.size(); qc.push_back(qs[i]); }
+        if (lead[(size_t)i] < 0) { pos[(size_t)i] = (int)qc.size(); qc.push_back(qs[i]); }
     int nc = (int)qc.size();
-    std::vector<int64_t> ride((size_t)nc * 4, 0);
+    std::vector<int32_t> riding((size_t)nc, 0), ride_q((size_t)nc * kMaxRide, -1), fill((size_t)nc, 0);
     for (int i = 0; i < nq; i++) {
         if (host[(size_t)i] < 0) continue;
-        const tm_query& q = qs[i];
-        int64_t cd = (int64_t)q.c * q.delta;
-        int64_t* r = &ride[(size_t)pos[(size_t)host[(size_t)i]] * 4];
-        r[0] = 1;
-        r[1] = q.delta;
-        r[2] = cd;
-        r[3] = -(int64_t)(draw(q.seed, 0, 0) % (uint64_t)cd);
+        int c = pos[(size_t)i], h = pos[(size_t)host[(size_t)i]];
+        riding[(size_t)c] = 1;
+        ride_q[(size_t)h * kMaxRide + fill[(size_t)h]++] = c;
     }
     std::vector<int32_t> nsub((size_t)nc, 0);
     std::vector<int64_t> sd((size_t)nc * kMaxSub, 0);
@@ -1940,37 +1923,15 @@ int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res
         nsub[(size_t)c] = std::max(nsub[(size_t)c], slot[(size_t)i] + 1);
     }
     std::vector<tm_result> rc_res((size_t)nc);
-    std::vector<unsigned long long> sc((size_t)nc * kMaxSub, 0), ro((size_t)nc * 3, 0);
+    std::vector<unsigned long long> sc((size_t)nc * kMaxSub, 0);
     BatchOut bo;
     bo.nsub = nsub.data();
     bo.sub_delta = sd.data();
     bo.sub_count = sc.data();
-    bo.ride = ride.data();
-    bo.ride_out = ro.data();
+    bo.riding = riding.data();
+    bo.ride_q = ride_q.data();
     int rc = run_batch_typed(g, qc.data(), nc, rc_res.data(), st, &bo);
     for (int i = 0; i < nq; i++) {
-        if (host[(size_t)i] >= 0) {
-            // the rider's result, folded as k_fold folds one shift with every window kept
-            const tm_query& q = qs[i];
-            int c = pos[(size_t)host[(size_t)i]];
-            const unsigned long long* a = &ro[(size_t)c * 3];
-            int64_t cd = (int64_t)q.c * q.delta;
-            int64_t J = 1 + (g->t_max + cd - 1) / cd;
-            tm_result r;
-            std::memset(&r, 0, sizeof(r));
-            r.status = rc_res[(size_t)c].status;
-            if (r.status == TM_OK && (a[2] >= (1ull << 63) || a[0] >= (1ull << 63))) r.status = TM_EOVERFLOW;
-            r.count = (int64_t)a[0];
-            double wd = (double)a[2] + (double)a[1] * 0x1.0p-64;
-            double zsum = 0.0;
-            zsum += wd / q.p;
-            r.estimate = zsum / 1;
-            r.windows = J;
-            r.windows_kept = J;
-            r.p_used = q.p;
-            res[i] = r;   // the enumeration, and so first_edges etc., is the exact query's
-            continue;
-        }
         if (lead[(size_t)i] < 0) {
             res[i] = rc_res[(size_t)pos[(size_t)i]];
             continue;

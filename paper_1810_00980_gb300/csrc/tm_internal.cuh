@@ -209,17 +209,16 @@ struct QPlan {
     int32_t wclamp;
     int64_t dsub[3];
     int64_t J_all;       // wclamp: the windows per shift (J is then 1 slot)
-    // an estimate of the same motif that keeps every window (p = 1, one shift) riding along
-    // with this exact query: each enumerated instance inside one of its windows and within
-    // its span adds its weight to r_acc = [count, weight lo, weight hi]
+    // estimates of the same motif riding along with this exact query: every instance this
+    // query enumerates is also added, with the rider's weight, to the rider's window when it
+    // lies inside a kept window of the rider and within the rider's span
     int32_t nride;
-    int32_t pad5;
-    int64_t r_delta, r_cd, r_shift;
-    const uint64_t* r_wtab;   // Q64 weights r_cd / (r_cd - dur), or null (long division)
-    unsigned long long* r_acc;
+    int32_t riding;      // 1: this estimate rides along with an exact query (no first edges)
+    int32_t ride_q[6];   // plan indices of the riders
     LevelPlan lv[TM_L_MAX];
 };
 constexpr int kMaxSub = 3;
+constexpr int kMaxRide = 6;
 
 struct Tuning {
     int block_threads = 256;
@@ -253,8 +252,8 @@ struct BatchOut {                 // optional per-window readback for one query
     int64_t shift = 0;
     const SegSpec* seg = nullptr; // per query, or null (whole graph)
     ShiftSums* sums = nullptr;    // host: per query, per shift (exact: one), or null
-    const int64_t* ride = nullptr;            // per query: [on, delta, c delta, shift] of a rider, or null
-    unsigned long long* ride_out = nullptr;   // host out: [nq][3] rider count, weight lo, weight hi
+    const int32_t* riding = nullptr;          // per query: 1 if it rides along (no first edges)
+    const int32_t* ride_q = nullptr;          // per query: [kMaxRide] plan indices of its riders, -1 unused
     const int32_t* nsub = nullptr;            // per query: spans counted alongside (exact)
     const int64_t* sub_delta = nullptr;       // [nq][kMaxSub]
     unsigned long long* sub_count = nullptr;  // host out: [nq][kMaxSub]

@@ -335,11 +335,14 @@ def test_prepared_batch_cuda_graph_matches_run_batch(tm, orc):
     want = tm.run_batch(g, qs, check=False)
     pb = tm.PreparedBatch(g, qs)
     st = torch.cuda.Stream()
+    keys = ("status", "count", "estimate", "windows", "windows_kept", "var_hat", "shift_var", "p_used")
     for rep in range(3):
         pb.launch(st.cuda_stream)
         got = pb.results(st.cuda_stream, check=False)
         for a, b in zip(got, want):
-            assert a == b
+            # (the work counters differ: in tm_run_batch, queries that ride along with another
+            # query's enumeration report none of their own)
+            assert {k: a[k] for k in keys} == {k: b[k] for k in keys}
     assert want[-1]["status"] == tm.TM_EINVAL
     assert want[0]["count"] == orc.count_exact(src, dst, t, *synth.MOTIFS["cycle3"], 3600, threads=8)
     pb.free()
@@ -658,10 +661,11 @@ def test_all_windows_kept_uses_whole_graph_pass(tm, orc):
         assert r["var_hat"] == 0.0
 
 
-def test_estimates_keeping_every_window_ride_along_exact_queries(tm, orc):
-    """An estimate with p = 1 (one shift) of the same three-edge motif as an exact query of
-    at least its span takes its instances from that query's enumeration: results equal the
-    estimate run alone (bit for bit) and the oracle's."""
+def test_estimates_ride_along_exact_queries(tm, orc):
+    """An estimate of the same three-edge motif as an exact query of at least its span takes
+    its instances from that query's enumeration (any p, b or q_j rule): results equal the
+    estimate run alone (bit for bit: counts, estimates, variance estimates, kept windows)
+    and the oracle's."""
     src, dst, t = synth.chung_lu_hawkes(2000, 150_000, 2.1, seed=33, horizon=4_000_000,
                                         max_degree=20_000, hub_bursts=4, burst_max=300)
     g = _graph(tm, src, dst, t)
@@ -672,9 +676,14 @@ def test_estimates_keeping_every_window_ride_along_exact_queries(tm, orc):
         qs += [tm.exact_query(mo, 86400), tm.exact_query(mo, 3600)]
         want += [("exact", orc.count_exact(src, dst, t, ms, md, 86400, threads=8)),
                  ("exact", orc.count_exact(src, dst, t, ms, md, 3600, threads=8))]
-        for (d, c, seed) in ((86400, 30, 3), (3600, 10, 4), (600, 5, 5)):
-            qs.append(tm.estimate_query(mo, d, c, 1.0, seed))
-            want.append(("est", orc.estimate(src, dst, t, ms, md, d, c, 1.0, seed, threads=8)))
+        for (d, c, p, seed, b) in ((86400, 30, 1.0, 3, 1), (3600, 10, 1.0, 4, 1), (600, 5, 1.0, 5, 1),
+                                   (3600, 10, 0.3, 6, 2), (600, 5, 0.5, 7, 1)):
+            qs.append(tm.estimate_query(mo, d, c, p, seed, b=b))
+            want.append(("est", orc.estimate(src, dst, t, ms, md, d, c, p, seed, b=b, threads=8)))
+        qs.append(tm.estimate_query(mo, 3600, 5, 20.0, 8, q_mode=tm.TM_Q_EDGES))
+        r_ = 20.0
+        qfun = lambda j, a, e, _t=t, _r=r_: min(1.0, _r * float(np.sum((_t - _t.min() >= a) & (_t - _t.min() <= e))) / len(_t))
+        want.append(("est", orc.estimate(src, dst, t, ms, md, 3600, 5, None, 8, q=qfun, threads=8)))
     res = tm.run_batch(g, qs)
     for q, r, (kind, w) in zip(qs, res, want):
         assert r["status"] == 0
@@ -685,3 +694,4 @@ def test_estimates_keeping_every_window_ride_along_exact_queries(tm, orc):
         alone = tm.run_batch(g, [q])[0]
         assert alone["count"] == r["count"] and alone["estimate"] == r["estimate"]
         assert alone["windows"] == r["windows"] and alone["windows_kept"] == r["windows_kept"]
+        assert alone["var_hat"] == r["var_hat"] and alone["shift_var"] == r["shift_var"]
