@@ -86,6 +86,11 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # let nvidia-smi start up (NVML initialisation) before the timed region begins, so
+            # that its start-up does not compete with the steps; it then samples every 200 ms
+            t_end = time.time() + 3.0
+            while not self.lines and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -335,7 +340,7 @@ def run_reference(args, rank):
            [(n, d, "estimate") for n in MOTIF_NAMES for d in DELTAS]
     vals = []
     for _ in range(max(args.steps, 1)):
-        cb = cpu_baseline(src, dst, t, meta, budget_s=max(10.0, 60.0 / max(args.steps, 1)))
+        cb = cpu_baseline(src, dst, t, meta, budget_s=max(5.0, 60.0 / max(args.steps, 1)))
         vals.append(cb["value"])
     v = statistics.median(vals)
     cb["value"] = v
@@ -509,7 +514,7 @@ def run_config5(args, tm, torch, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
