@@ -82,7 +82,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.index)],
+                                          "-lms", "100", "-i", str(self.index)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -97,7 +97,10 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
 
     def __exit__(self, *a):
         if self.proc:
@@ -109,10 +112,12 @@ class ClockSampler:
             if self.thread:
                 self.thread.join(timeout=2)
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Samples taken between host times t0 and t1 (the timed region), else all."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for (ts, ln) in self.lines if t0 is not None and t0 <= ts <= t1]
+        for ln in (inside or [ln for _, ln in self.lines]):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -399,11 +404,14 @@ def run_config3(args, tm, torch, world, rank):
     e1 = torch.cuda.Event(enable_timing=True)
     match_ms = []
     with ClockSampler(torch.cuda.current_device()) as clk:
+        clk_t0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
             b = step()
             match_ms.append(tm.profile_last()["match_ms"])
         e1.record(stream)
+        torch.cuda.synchronize()
+        clk_t1 = time.time()
         torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
     if world > 1:
@@ -431,7 +439,7 @@ def run_config3(args, tm, torch, world, rank):
         "first_edges_per_step": sum(r["first_edges"] for r in results),
         "roofline": {"kernel": "k_match", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "algorithmic_bytes": b_match, "launch_ms": mm},
-        "gpu_launches": launches, "clocks": clk.summary(),
+        "gpu_launches": launches, "clocks": clk.summary(clk_t0, clk_t1),
     }
     print(json.dumps(out))
 
@@ -468,6 +476,7 @@ def run_config5(args, tm, torch, world, rank):
     e1 = torch.cuda.Event(enable_timing=True)
     prof = []
     with ClockSampler(torch.cuda.current_device()) as clk:
+        clk_t0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
             b, pg = step()
@@ -475,6 +484,8 @@ def run_config5(args, tm, torch, world, rank):
             p["graph_ms"] = pg
             prof.append(p)
         e1.record(stream)
+        torch.cuda.synchronize()
+        clk_t1 = time.time()
         torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
     results = b.results()
@@ -506,7 +517,7 @@ def run_config5(args, tm, torch, world, rank):
                       for k in ("graph_ms", "windows_ms", "level2_ms", "match_ms", "fold_ms")},
         "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "algorithmic_bytes": kb, "launch_ms": kms},
-        "gpu_launches": launches, "clocks": clk.summary(),
+        "gpu_launches": launches, "clocks": clk.summary(clk_t0, clk_t1),
     }
     print(json.dumps(out))
 
@@ -622,6 +633,7 @@ def main():
     step_ms = []
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
+        clk_t0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
             s0 = torch.cuda.Event(enable_timing=True)
@@ -636,6 +648,8 @@ def main():
             s1.synchronize()
             step_ms.append(s0.elapsed_time(s1))
         e1.record(stream)
+        torch.cuda.synchronize()
+        clk_t1 = time.time()
         torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
     launches = tm.profile_last()["launches"] - launches0
@@ -789,7 +803,7 @@ def main():
         "stream": stream_res,
         "q_corr_edges_vs_weight": q_corr,
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clk.summary(clk_t0, clk_t1),
     }
     print(json.dumps(out))
     if world > 1:
