@@ -695,3 +695,31 @@ def test_estimates_ride_along_exact_queries(tm, orc):
         assert alone["count"] == r["count"] and alone["estimate"] == r["estimate"]
         assert alone["windows"] == r["windows"] and alone["windows_kept"] == r["windows_kept"]
         assert alone["var_hat"] == r["var_hat"] and alone["shift_var"] == r["shift_var"]
+
+
+def test_sharing_limits_and_mixes(tm, orc):
+    """Batches that stretch the sharing rules: more spans than one leader carries, more
+    estimates than riders allowed, equal spans, a rejected query, automatic p and q_j rules
+    side by side -- every result equals the query run alone."""
+    src, dst, t = synth.chung_lu_hawkes(1500, 80_000, 2.1, seed=37, horizon=3_000_000)
+    g = _graph(tm, src, dst, t)
+    mo = tm.Motif(*synth.MOTIFS["cycle3"])
+    mo2 = tm.Motif(*synth.MOTIFS["outstar3"])
+    qs = [tm.exact_query(mo, d) for d in (86400, 600, 3600, 3600, 7200, 100, 0)]
+    qs += [tm.estimate_query(mo, d, c, p, s, b=b) for (d, c, p, s, b) in
+           ((3600, 10, 0.4, 1, 1), (3600, 10, 0.4, 2, 3), (600, 30, 0.9, 3, 1), (86400, 2, 0.2, 4, 1),
+            (7200, 5, 1.0, 5, 1), (100, 10, 0.5, 6, 2), (3600, 3, 0.7, 7, 1), (120000, 10, 0.5, 8, 1))]
+    qs.append(tm.estimate_query(mo, 3600, 10, 0.05, 9, b=2, q_mode=tm.TM_Q_AUTO))
+    qs.append(tm.estimate_query(mo, 3600, 10, 15.0, 10, q_mode=tm.TM_Q_EDGES))
+    qs.append(tm.Query(mo, -3))                                  # rejected
+    qs += [tm.exact_query(mo2, 3600), tm.estimate_query(mo2, 3600, 10, 0.5, 11),
+           tm.estimate_query(mo2, 600, 10, 0.5, 12, b=2)]
+    res = tm.run_batch(g, qs, check=False)
+    keys = ("status", "count", "estimate", "windows", "windows_kept", "var_hat", "shift_var", "p_used")
+    for q, r in zip(qs, res):
+        alone = tm.run_batch(g, [q], check=False)[0]
+        assert {k: r[k] for k in keys} == {k: alone[k] for k in keys}, (q.mode, q.delta, q.p, r, alone)
+    assert res[17]["status"] == tm.TM_EINVAL
+    ms, md = synth.MOTIFS["cycle3"]
+    for q, r in zip(qs[:7], res[:7]):
+        assert r["count"] == orc.count_exact(src, dst, t, ms, md, q.delta, threads=8)
