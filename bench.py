@@ -138,7 +138,7 @@ class ClockSampler:
 # -------------------------------------------------------------- workload ---
 def make_graph():
     from paper_1810_00980_gb300 import synth
-    return synth.config2_graph(seed=SEED)
+    return synth.bursty_100k_10m_graph(seed=SEED)
 
 
 def make_queries(tm):
@@ -162,7 +162,7 @@ SERVE_MOTIFS = ("cycle3", "outstar3", "pingpong", "cycle4")
 
 
 def serve_mix(tm, motifs, gids, rng, n):
-    """Config-4 style query stream: graph, motif, delta, exact or estimate
+    """Served query stream: graph, motif, delta, exact or estimate
     (c in {10, 30}, p in {0.01, 0.05, 0.1}) and seed drawn uniformly."""
     qs = []
     for _ in range(n):
@@ -358,14 +358,14 @@ def run_reference(args, rank):
     print(json.dumps(out))
 
 
-def run_config3(args, tm, torch, world, rank):
+def run_bursty_100m_4cycle(args, tm, torch, world, rank):
     """Batched estimator workload: Chung-Lu (exponent 2.0) + Hawkes, N = 1e6,
     M = 1e8; the 4-cycle a->b->c->d->a at delta = 3,600 s; c in {10, 30, 100} x
     p in {0.01, 0.1} x 32 seeds = 192 estimate queries in one batched launch per
     step (after the graph ingest and adjacency build).  Errors against the
     exact count, per (c, p): mean over seeds and the error of the 32-seed mean."""
     from paper_1810_00980_gb300 import synth
-    src, dst, t = synth.config3_graph()
+    src, dst, t = synth.bursty_1m_100m_graph()
     M = len(t)
     d_src, d_dst, d_t = (torch.from_numpy(x).cuda() for x in (src, dst, t))
     stream = torch.cuda.Stream()
@@ -431,7 +431,7 @@ def run_config3(args, tm, torch, world, rank):
         "metric": METRIC, "value": world * len(qs) * args.steps / (total_ms / 1e3), "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "config 3: Chung-Lu exponent 2.0 + Hawkes, N=1,000,000, M=100,000,000, 2 years; "
+        "config": {"workload": "Chung-Lu exponent 2.0 + Hawkes, N=1,000,000, M=100,000,000, 2 years; "
                                "4-cycle, delta=3600; c {10,30,100} x p {0.01,0.1} x 32 seeds = 192 estimate "
                                "queries in one batched launch; graph ingest + adjacency build per step",
                    "queries_per_step": len(qs), "edges": M, "l2": "inputs larger than L2"},
@@ -444,13 +444,13 @@ def run_config3(args, tm, torch, world, rank):
     print(json.dumps(out))
 
 
-def run_config5(args, tm, torch, world, rank):
+def run_hubs_1b_outstar(args, tm, torch, world, rank):
     """Hub-skewed stress: N = 1e7, M = 1e9 (Chung-Lu 1.8 capped at degree 5e6,
     Hawkes times, 1,000 hub bursts of up to 1e4 edges in 60 s), drawn on the
     GPU; the out-star at delta = 1,800 s estimated with c = 30, p = 0.01 for 8
     seeds in one batched launch per step (after the graph ingest and build)."""
     from paper_1810_00980_gb300 import synth
-    d_src, d_dst, d_t = synth.config5_graph_gpu()
+    d_src, d_dst, d_t = synth.hub_bursty_10m_1b_graph_gpu()
     torch.cuda.synchronize()
     M = int(d_t.numel())
     stream = torch.cuda.Stream()
@@ -505,7 +505,7 @@ def run_config5(args, tm, torch, world, rank):
         "metric": METRIC, "value": world * len(qs) * args.steps / (total_ms / 1e3), "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "config 5: Chung-Lu exponent 1.8 capped at degree 5e6, N=10,000,000, "
+        "config": {"workload": "Chung-Lu exponent 1.8 capped at degree 5e6, N=10,000,000, "
                                "M=1,000,000,000, Hawkes + 1,000 hub bursts of <=1e4 edges in 60 s; out-star, "
                                "delta=1800, c=30, p=0.01, 8 seeds in one batched launch; graph ingest + "
                                "adjacency build per step", "queries_per_step": len(qs), "edges": M,
@@ -534,7 +534,7 @@ def main():
                     help="serving run on four resident graphs of 1M, 10M, 25M and 50M edges")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-stream", action="store_true", help="skip the host-streaming measurement")
-    ap.add_argument("--workload", default="config2", choices=["config2", "config3", "config5"])
+    ap.add_argument("--workload", default="bursty-10m", choices=["bursty-10m", "bursty-100m-4cycle", "hubs-1b"])
     ap.add_argument("--tuning", default="auto",
                     help="'auto' (autotune on the batch) or block_threads,blocks_per_sm,chunk_items,enum_threshold")
     ap.add_argument("--calibrate", action="store_true",
@@ -559,8 +559,8 @@ def main():
     __graft_entry__.build()
     from paper_1810_00980_gb300 import tm
 
-    if args.workload in ("config3", "config5"):
-        (run_config3 if args.workload == "config3" else run_config5)(args, tm, torch, world, rank)
+    if args.workload in ("bursty-100m-4cycle", "hubs-1b"):
+        (run_bursty_100m_4cycle if args.workload == "bursty-100m-4cycle" else run_hubs_1b_outstar)(args, tm, torch, world, rank)
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()

@@ -221,18 +221,18 @@ def clique_reduction(n: int, edges, k: int):
 
 
 # Workloads with the sizes of the configurations this library is measured on.
-def config1_graph(seed: int = 1):
+def uniform_1k_graph(seed: int = 1):
     """N=1,000, M=20,000, uniform endpoints, t ~ U{0..999,999}."""
     return uniform_graph(1_000, 20_000, 1_000_000, seed)
 
 
-def config2_graph(seed: int = 2, m_edges: int = 10_000_000, n_nodes: int = 100_000):
+def bursty_100k_10m_graph(seed: int = 2, m_edges: int = 10_000_000, n_nodes: int = 100_000):
     """Chung-Lu (exponent 2.1) + Hawkes times over two years; N=1e5, M=1e7."""
     return chung_lu_hawkes(n_nodes, m_edges, 2.1, seed)
 
 
-def config3_graph(seed: int = 3, m_edges: int = 100_000_000, n_nodes: int = 1_000_000):
-    """As config2_graph with exponent 2.0; N=1e6, M=1e8."""
+def bursty_1m_100m_graph(seed: int = 3, m_edges: int = 100_000_000, n_nodes: int = 1_000_000):
+    """As bursty_100k_10m_graph with exponent 2.0; N=1e6, M=1e8."""
     return chung_lu_hawkes(n_nodes, m_edges, 2.0, seed)
 
 
@@ -350,7 +350,7 @@ def chung_lu_hawkes_gpu(n_nodes: int, m_edges: int, gamma: float, seed: int,
     return src, dst, t
 
 
-def config5_graph_gpu(seed: int = 5, m_edges: int = 1_000_000_000, n_nodes: int = 10_000_000,
+def hub_bursty_10m_1b_graph_gpu(seed: int = 5, m_edges: int = 1_000_000_000, n_nodes: int = 10_000_000,
                       device: str = "cuda"):
     """N=1e7, M=1e9, Chung-Lu exponent 1.8 with the maximum expected degree
     capped at 5e6, Hawkes times over two years, and 1,000 hub bursts of up to

@@ -178,7 +178,7 @@ def test_edge_cases(tm, orc):
 
 
 def test_device_and_host_load_agree(tm):
-    src, dst, t = synth.config1_graph()
+    src, dst, t = synth.uniform_1k_graph()
     a = _graph(tm, src, dst, t, device=True)
     b = _graph(tm, src, dst, t, device=False)
     ia, ib = a.info(), b.info()
@@ -204,10 +204,10 @@ def _check_windows(tm, orc, g, src, dst, t, ms, md, delta, c, p, seed, k=0):
     return recs
 
 
-def test_config1_exact_and_estimate(tm, orc):
-    """Config 1 in full: N=1,000, M=20,000 uniform; cycle, delta=3,600;
+def test_uniform_20k_exact_and_estimate(tm, orc):
+    """Uniform graph in full: N=1,000, M=20,000; cycle, delta=3,600;
     estimate with c=30, p=0.1, seed 1."""
-    src, dst, t = synth.config1_graph()
+    src, dst, t = synth.uniform_1k_graph()
     g = _graph(tm, src, dst, t)
     ms, md = synth.MOTIFS["cycle3"]
     mo = tm.Motif(ms, md)
@@ -287,12 +287,12 @@ def test_variance_estimate_is_lemma44(tm, orc):
 
 # --------------------------------------------------- full size, sampled -----
 @pytest.mark.slow
-def test_config2_full_size_sampled_windows(tm, orc):
-    """Config 2 size (N=1e5, M=1e7, Chung-Lu 2.1 + Hawkes): the batched path in
+def test_bursty_10m_full_size_sampled_windows(tm, orc):
+    """Full size N=1e5, M=1e7 (Chung-Lu 2.1 + Hawkes): the batched path in
     the benchmark's launch configuration; per-window exact counts and weights of
     sampled kept windows checked one by one against the oracle, and one full
     exact count."""
-    src, dst, t = synth.config2_graph()
+    src, dst, t = synth.bursty_100k_10m_graph()
     g = _graph(tm, src, dst, t)
     tn = t - t.min()
     for name in ("cycle3", "outstar3", "pingpong"):
@@ -384,13 +384,13 @@ def test_wide_time_span_uses_64_bit_times(tm, orc):
 
 
 @pytest.mark.slow
-def test_config3_full_size_sampled_windows(tm, orc):
-    """Config 3 size (N=1e6, M=1e8, Chung-Lu 2.0 + Hawkes): the 4-cycle at
+def test_bursty_100m_full_size_sampled_windows(tm, orc):
+    """Full size N=1e6, M=1e8 (Chung-Lu 2.0 + Hawkes): the 4-cycle at
     delta=3600 in the batched launch the benchmark times (all c x p x seed
     combinations of one shift each in one batch); per-window exact counts and
     weights of sampled kept windows checked one by one against the oracle."""
     import torch
-    src, dst, t = synth.config3_graph()
+    src, dst, t = synth.bursty_1m_100m_graph()
     g = _graph(tm, src, dst, t)
     tn = t - t.min()
     ms, md = synth.MOTIFS["cycle4"]
@@ -420,15 +420,15 @@ def test_config3_full_size_sampled_windows(tm, orc):
 
 
 @pytest.mark.slow
-def test_config5_full_size_sampled_windows(tm, orc):
-    """Config 5 size (N=1e7, M=1e9, Chung-Lu 1.8 capped at degree 5e6, Hawkes
+def test_hubs_1b_full_size_sampled_windows(tm, orc):
+    """Full size N=1e7, M=1e9 (Chung-Lu 1.8 capped at degree 5e6, Hawkes
     times plus 1,000 hub bursts of up to 1e4 edges in 60 s), drawn on the GPU:
     the out-star at delta=1800 estimated with c=30, p=0.01 for 8 seeds in one
     batched launch; sampled kept windows checked one by one against the oracle.
     Windows holding a hub burst are not sampled (the oracle's enumeration is
     cubic in a burst; bursts are checked at smaller scale in test_hub_heavy_graph)."""
     import torch
-    d_src, d_dst, d_t = synth.config5_graph_gpu()
+    d_src, d_dst, d_t = synth.hub_bursty_10m_1b_graph_gpu()
     g = tm.Graph(d_src, d_dst, d_t)
     ms, md = synth.MOTIFS["outstar3"]
     mo = tm.Motif(ms, md)

@@ -8,7 +8,7 @@ from paper_1810_00980_gb300 import synth
 
 def test_uniform_graph_is_seeded_and_sorted():
     a = synth.uniform_graph(1000, 20_000, 1_000_000, 1)
-    b = synth.config1_graph(1)
+    b = synth.uniform_1k_graph(1)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
     src, dst, t = a
