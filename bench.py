@@ -484,6 +484,9 @@ def run_hubs_1b_outstar(args, tm, torch, world, rank):
     for _ in range(args.warmup):
         b, _ = step()
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     launches0 = tm.profile_last()["launches"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
