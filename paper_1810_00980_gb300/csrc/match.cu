@@ -755,6 +755,23 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                             int64_t hi = gallop_ub(G.pair_t, ha, hh, t1 + Q.dsub[i]);
                             acc.s(A_X0 + i) += (unsigned long long)((__ldg(S + hi) - sa) - (hi - ha) * le2);
                         }
+                        if (Q.nride) {
+                            // estimates riding along need the last edges one by one, up to the
+                            // latest end of a kept rider window holding t1
+                            int64_t thr = t1;
+                            for (int r = 0; r < Q.nride; r++) {
+                                const QPlan& R = PL[Q.ride_q[r]];
+                                for (int k = 0; k < R.b; k++) {
+                                    int64_t w, th;
+                                    ride_window(R, k, t1, w, th);
+                                    if (A.W.kept[w]) thr = max(thr, th);
+                                }
+                            }
+                            if (thr > t1) {
+                                len = gallop_ub(G.pair_t, ha, hh, thr) - ha;   // items for the riders only
+                                hh = le2;
+                            }
+                        }
                     } else {
                         len = hh - ha;   // items: the last edges; k_match reads ha and le2
                         hh = le2;
@@ -1069,12 +1086,17 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     int64_t j = A.hs_a[f] + (w - A.excl[f]);
                     int64_t t3 = __ldg(G.pair_t + j);
                     int64_t cnt = (__ldg(S + j + 1) - __ldg(S + j)) - A.hs_hi[f];
-                    acc_switch(acc, win, A.W.acc);
-                    acc.s(A_CAND) += 1;
-                    acc.s(A_LAST) += 1;
-                    if (cnt > 0) {
-                        acc.f[A_COUNT] += cnt;
-                        if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                    if (Q.mode == TM_MODE_EXACT) {
+                        // the query's own count came from the tables: the items are its riders'
+                        if (cnt > 0 && Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
+                    } else {
+                        acc_switch(acc, win, A.W.acc);
+                        acc.s(A_CAND) += 1;
+                        acc.s(A_LAST) += 1;
+                        if (cnt > 0) {
+                            acc.f[A_COUNT] += cnt;
+                            add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                        }
                     }
                 } else if (l2 < 0 && Q.hoist) {
                     // closing edge e3 of the first edge's pair: count the valid second
@@ -1889,11 +1911,10 @@ int run_batch_once(const tm_graph* g, const tm_query* qs, int nq, tm_result* res
         const tm_query& q = qs[i];
         std::string why;
         if (q.mode != TM_MODE_ESTIMATE || (q.q_mode != TM_Q_UNIFORM && q.q_mode != TM_Q_EDGES)) continue;
-        if (!q.motif || q.motif->l != 3 || q.motif->k == 2 || q.motif->lv[2].view != kPair) continue;
+        if (!q.motif || q.motif->l != 3 || q.motif->lv[2].view != kPair) continue;
         if (validate_query(g, q, why) != TM_OK) continue;
         for (int L : heads)
-            if (nrid[(size_t)L] < kMaxRide && qs[L].motif->k != 2 && qs[L].delta >= q.delta &&
-                same_motif(qs[L].motif, q.motif)) {
+            if (nrid[(size_t)L] < kMaxRide && qs[L].delta >= q.delta && same_motif(qs[L].motif, q.motif)) {
                 host[(size_t)i] = L;
                 nrid[(size_t)L]++;
                 any = true;
