@@ -492,7 +492,6 @@ __device__ __forceinline__ const QPlan* stage_plans(const QPlan* gplans, int nq,
     return reinterpret_cast<const QPlan*>(smem);
 }
 
-size_t plan_smem_bytes(int nq) { return nq <= kSmemPlans ? sizeof(QPlan) * (size_t)nq : 0; }
 static_assert(kSmemPlans == 64, "acc_smem_offset assumes 64 staged plans at most");
 
 // dynamic shared memory of k_level2 / k_match: plans, then the accumulator slots
@@ -1129,63 +1128,82 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                         if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
                         if (Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
                     }
-                } else if (l2 < 0) {
-                    // closing-edge candidate e3 = (x, t3); count second edges in (t1, t3)
+                } else {
+                // Two item kinds end in a count of one pair's entries in a time range: a
+                // closing-edge candidate e3 = (x, t3) counts second edges in (t1, t3); a
+                // second-edge candidate of an exact three-edge query counts closing edges in
+                // (tc, thi].  Their pair lookups go through one call site, so that a warp
+                // holding both kinds waits on one chain of dependent loads, not two.
+                int kind = 0;   // 1: closing-edge candidate, 2: second edge closed by range
+                int32_t pu = 0, pv = 0;
+                int64_t plo = 0, pthi = 0, t3 = 0;
+                bool ok = false;
+                acc_switch(acc, win, A.W.acc);
+                acc.s(A_CAND) += 1;
+                if (l2 < 0) {
                     const LevelPlan L = Q.lv[2];
                     const LevelPlan M1 = Q.lv[1];
                     int64_t c = (-1 - l2) + (w - A.excl[f]);
                     bool x_src = L.su == 2;
                     int32_t x = x_src ? __ldg(G.in_nbr + c) : __ldg(G.out_nbr + c);
-                    int64_t t3 = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
-                    acc_switch(acc, win, A.W.acc);
-                    acc.s(A_CAND) += 1;
+                    t3 = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
                     if (x != phi[0] && x != phi[1]) {
-                        int32_t mu = M1.su == 2 ? x : phi_get(phi, M1.su);
-                        int32_t mv = M1.sv == 2 ? x : phi_get(phi, M1.sv);
-                        int64_t cnt = pair_count(G, mu, mv, t1, t3 - 1);
-                        acc.s(A_LAST) += 1;
-                        if (cnt) {
-                            acc.f[A_COUNT] += cnt;
-                            if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
-                            if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
-                            if (Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
-                        }
+                        kind = 1;
+                        pu = M1.su == 2 ? x : phi_get(phi, M1.su);
+                        pv = M1.sv == 2 ? x : phi_get(phi, M1.sv);
+                        plo = t1;
+                        pthi = t3 - 1;
                     }
                 } else {
-                const LevelPlan P = Q.lv[1];
-                int32_t s, d;
-                read_cand(G, P, phi, l2 + (w - A.excl[f]), s, d, tc);
-                bool ok = check_bind(P, phi, s, d);
-                if (Q.hoist) {
-                    ha = A.hs_a[f];
-                    hh = A.hs_hi[f];
-                }
-                acc_switch(acc, win, A.W.acc);
-                if (Q.l == 2) {
-                    acc.s(A_INST) += 1;
-                    if (ok) {
-                        acc.f[A_COUNT] += 1;
-                        if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - t1);
+                    const LevelPlan P = Q.lv[1];
+                    int32_t s, d;
+                    read_cand(G, P, phi, l2 + (w - A.excl[f]), s, d, tc);
+                    ok = check_bind(P, phi, s, d);
+                    if (Q.hoist) {
+                        ha = A.hs_a[f];
+                        hh = A.hs_hi[f];
                     }
-                } else {
-                    acc.s(A_CAND) += 1;
                     const LevelPlan L = Q.lv[2];
-                    if (ok && Q.l == 3 && Q.mode == TM_MODE_EXACT && L.view == kPair) {
-                        // close the instance here: the last edge is counted by range length
-                        int64_t clo, chi;
-                        if (Q.hoist) {
-                            clo = upper_bound_i64(G.pair_t, ha, hh, tc);
-                            chi = hh;
-                        } else {
-                            pair_range(G, phi_get(phi, L.su), phi_get(phi, L.sv), tc, thi, clo, chi);
+                    if (Q.l == 2) {
+                        acc.s(A_CAND) -= 1;
+                        acc.s(A_INST) += 1;
+                        if (ok) {
+                            acc.f[A_COUNT] += 1;
+                            if (Q.mode == TM_MODE_ESTIMATE) add_weight(acc, Q, tc - t1);
                         }
-                        acc.f[A_COUNT] += chi - clo;
-                        acc.s(A_LAST) += 1;
-                        if (Q.nsub && chi > clo) add_sub_range(acc, Q, G.pair_t, clo, chi, t1);
-                        if (Q.nride && chi > clo) ride_range(PL, Q, A.W.kept, A.W.acc, G.pair_t, clo, chi, t1, tc);
+                    } else if (ok && Q.l == 3 && Q.mode == TM_MODE_EXACT && L.view == kPair) {
+                        kind = 2;
+                        pu = phi_get(phi, L.su);
+                        pv = phi_get(phi, L.sv);
+                        plo = tc;
+                        pthi = thi;
                     } else {
                         deeper = ok;
                     }
+                }
+                // the pair lookup: the hoisted closing range is already known
+                int64_t clo = 0, chi = 0;
+                if (kind == 2 && Q.hoist) {
+                    clo = upper_bound_i64(G.pair_t, ha, hh, tc);
+                    chi = hh;
+                } else if (kind) {
+                    pair_range(G, pu, pv, plo, pthi, clo, chi);
+                }
+                if (kind == 1) {
+                    int64_t cnt = chi - clo;
+                    acc.s(A_LAST) += 1;
+                    if (cnt) {
+                        acc.f[A_COUNT] += cnt;
+                        if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
+                        if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
+                        if (Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
+                    }
+                } else if (kind == 2) {
+                    // close the instance here: the last edge is counted by range length
+                    acc.f[A_COUNT] += chi - clo;
+                    acc.s(A_LAST) += 1;
+                    if (Q.nsub && chi > clo) add_sub_range(acc, Q, G.pair_t, clo, chi, t1);
+                    if (Q.nride && chi > clo) ride_range(PL, Q, A.W.kept, A.W.acc, G.pair_t, clo, chi, t1, tc);
                 }
                 }
             }
