@@ -1541,6 +1541,16 @@ int ex_tables_for(const tm_graph* g, const std::vector<QPlan>& hp, cudaStream_t 
     return ensure_ex_tables(const_cast<tm_graph*>(g), st, need_own, need_rev, &G.ex_own, &G.ex_rev);
 }
 
+// per-first-edge scratch of one batch: window, second-level range start and length, the
+// exclusive scan of the lengths, the hoisted closing ranges, and the block-window and
+// chunk-start tables
+size_t per_first_scratch_bytes(int64_t F, bool hoist) {
+    size_t Fs = (size_t)std::max<int64_t>(F, 1);
+    size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
+    return 2 * a256(4 * Fs) + (hoist ? 4 : 2) * a256(8 * Fs) + a256(4 * nbw) + a256(8 * ncf);
+}
+constexpr size_t kBoundScratchBytes = (size_t)2 << 30;
+
 template <typename TT>
 int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
                 BatchOut* dbg) {
@@ -1550,7 +1560,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     std::vector<QPlan> hp((size_t)nq);
     std::vector<int> qstat((size_t)nq, TM_OK);
     int first_err = TM_OK;
-    int64_t NW = 0, n_sums = 0;
+    int64_t NW = 0, n_sums = 0, F_ub = 0;
     int lmax = 1, kmax = 2;
     bool any_hoist = false, any_full = false;
     size_t wtab_bytes = 0, full_bytes = 0;
@@ -1603,6 +1613,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         }
         hp[(size_t)i].win_base = NW;
         hp[(size_t)i].sum_base = n_sums;
+        if (!hp[(size_t)i].riding)   // at most m first edges per exact query and per shift
+            F_ub += hp[(size_t)i].mode == TM_MODE_EXACT ? g->m : (int64_t)hp[(size_t)i].b * g->m;
         n_sums += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].b;
         NW += hp[(size_t)i].mode == TM_MODE_EXACT ? 1 : hp[(size_t)i].J * hp[(size_t)i].b;
         lmax = std::max(lmax, hp[(size_t)i].l);
@@ -1715,19 +1727,22 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         fail(cudaGetLastError(), "k_windows");
     }
     if (rc == TM_OK) rc = scan_exclusive_i64(W.nfirst, W.fbase, NW, dF, st);
+    // The per-first-edge scratch is sized for the bound on F when that fits in
+    // kBoundScratchBytes, and the kernels read F on the device: no host round trip
+    // between the window partition and the matcher.  Otherwise F is read back first.
+    const bool bounded = F_ub > 0 && per_first_scratch_bytes(F_ub, any_hoist) <= kBoundScratchBytes;
     int64_t F = 0;
     ev_w1 = pe.mark(st);
-    if (rc == TM_OK) {
+    if (rc == TM_OK && !bounded) {
         fail(cudaMemcpyAsync(&F, dF, 8, cudaMemcpyDeviceToHost, st), "F readback");
         fail(cudaStreamSynchronize(st), "sync F");
     }
+    const int64_t Fa = bounded ? F_ub : F;   // first edges the scratch holds
     char* fb = nullptr;
-    if (rc == TM_OK && F > 0) {
-        size_t Fs = (size_t)F;
+    if (rc == TM_OK && Fa > 0) {
+        size_t Fs = (size_t)Fa;
         size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
-        fail(cudaMallocAsync((void**)&fb, a256(4 * Fs) + (any_hoist ? 5 : 3) * a256(8 * Fs) + a256(4 * nbw) +
-                                              a256(8 * ncf) + a256(4 * Fs), st),
-             "per-edge scratch");
+        fail(cudaMallocAsync((void**)&fb, per_first_scratch_bytes(Fa, any_hoist), st), "per-edge scratch");
         if (rc == TM_OK) {
             char* q2 = fb;
             auto take2 = [&](size_t bytes) { char* r = q2; q2 += a256(bytes); return (void*)r; };
@@ -1740,25 +1755,26 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             int32_t* bwin = (int32_t*)take2(4 * nbw);
             int64_t* cf = (int64_t*)take2(8 * ncf);
             MatchArgs<TT> A;
-            A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = F; A.d_F = nullptr;
+            const int64_t* d_Fk = bounded ? dF : nullptr;
+            A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = Fa; A.d_F = d_Fk;
             A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
             A.d_W2 = dW2; A.counter = dctr;
             A.enum_threshold = tu.enum_threshold;
             A.chunk = tu.chunk_items;
             A.blockwin = bwin; A.chunkf = cf; A.nchunkf = (int64_t)ncf;
             int bt = tu.block_threads;
-            int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
+            int64_t gl2 = std::min<int64_t>((Fa + 255) / 256, (int64_t)nsm * 8);
             k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
-                W.fbase, NW, F, nullptr, bwin);
+                W.fbase, NW, Fa, d_Fk, bwin);
             count_launch();
             ev_l0 = pe.mark(st);
             k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, len32, lo2, hs_a, hs_hi); count_launch();
             fail(cudaGetLastError(), "k_level2");
             ev_l2 = pe.mark(st);
-            if (rc == TM_OK) rc = scan_lengths(len32, excl, F, nullptr, dW2, nullptr, 0, st);
+            if (rc == TM_OK) rc = scan_lengths(len32, excl, Fa, d_Fk, dW2, nullptr, 0, st);
             if (rc == TM_OK) {
                 k_chunkf<<<(unsigned)std::min<int64_t>(((int64_t)ncf + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
-                    excl, F, nullptr, dW2, A.chunk, (int64_t)ncf, cf);
+                    excl, Fa, d_Fk, dW2, A.chunk, (int64_t)ncf, cf);
                 count_launch();
                 fail(cudaGetLastError(), "k_chunkf");
             }
@@ -1778,6 +1794,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 fail(cudaGetLastError(), "k_match");
                 ev_m1 = pe.mark(st);
                 if (pe.on) fail(cudaMemcpyAsync(&hW2, dW2, 8, cudaMemcpyDeviceToHost, st), "W2");
+                if (pe.on && bounded) fail(cudaMemcpyAsync(&F, dF, 8, cudaMemcpyDeviceToHost, st), "F");
             }
         }
     }
