@@ -312,7 +312,9 @@ typedef struct {
 } tm_profile;
 int tm_profile_enable(int32_t on);
 /* Return device memory that freed graphs and batch scratch left in the library's
- * stream-ordered pool (kept mapped for reuse) to the device.  Synchronises the device. */
+ * stream-ordered pool (kept mapped for reuse) to the device, with the grow-only scratch
+ * buffers (up to four per device, each as large as the largest graph build or batch
+ * scratch it served) that no running call holds.  Synchronises the device. */
 int tm_release_cached_memory(void);
 int tm_profile_last(tm_profile* out);
 

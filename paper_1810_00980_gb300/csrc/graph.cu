@@ -368,15 +368,15 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     int64_t *head, *pid, *dP;
     // index path: 6 u32 + 2 i64 per edge; payload path (32-bit times): 3 u32 + 3 u64
     size_t scratch = std::max(6 * align256(4 * M) + 2 * sz_i64m, 3 * align256(4 * M) + 3 * sz_i64m) + 256;
-    char* sb = nullptr;
-    e = cudaMallocAsync((void**)&sb, scratch, st);
-    if (e != cudaSuccess) {
+    ScratchLease lease;
+    int lrc = scratch_acquire(scratch, st, lease);
+    if (lrc != TM_OK) {
         cudaStreamSynchronize(st);
         pool_free(g->block, dev);
         delete g;
-        return cuda_status(e, "cudaMallocAsync(graph scratch)", __FILE__, __LINE__);
+        return lrc;
     }
-    char* q = sb;
+    char* q = (char*)lease.p;
     auto takes = [&](size_t bytes) { char* r = q; q += align256(bytes); return (void*)r; };
     ks = (uint32_t*)takes(4 * M);
     kd = (uint32_t*)takes(4 * M);
@@ -386,7 +386,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     vt = (uint32_t*)takes(4 * M);
     head = (int64_t*)takes(8 * M);
     pid = (int64_t*)takes(8 * M);
-    dP = (int64_t*)(sb + scratch - 256);
+    dP = (int64_t*)((char*)lease.p + scratch - 256);
 
     int bits = bits_for(n);
     unsigned gr = grid_for(m);
@@ -409,7 +409,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     uint32_t* psrc = nullptr;   // pair sources (the hash keys), in pair order
     if (tb == 4) {
         // payload path: scratch laid out as three u32 and three u64 arrays
-        char* q2 = sb;
+        char* q2 = (char*)lease.p;
         auto take2 = [&](size_t bytes) { char* r = q2; q2 += align256(bytes); return (void*)r; };
         uint32_t* k0 = (uint32_t*)take2(4 * M);
         uint32_t* k1 = (uint32_t*)take2(4 * M);
@@ -543,7 +543,7 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
             if (rc == TM_OK && pe.on) store_profile_graph(pe.ms(ev0, ev1));
         }
     }
-    cudaFreeAsync(sb, st);
+    scratch_release(lease, st);
     if (rc != TM_OK) {
         cudaStreamSynchronize(st);
         pool_free(g->block, dev);
@@ -645,21 +645,23 @@ int tm_graph_load(const int32_t* src, const int32_t* dst, const int64_t* t, int6
     if (m > 0 && (!src || !dst || !t)) { tmo::set_error("NULL edge array"); return TM_EINVAL; }
     cudaStream_t st;
     TM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    int32_t *ds = nullptr, *dd = nullptr;
-    int64_t* dt = nullptr;
     size_t M = (size_t)(m > 0 ? m : 1);
-    int rc = TM_OK;
-    cudaError_t e = cudaMallocAsync((void**)&ds, 4 * M, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&dd, 4 * M, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&dt, 8 * M, st);
+    tmo::ScratchLease lease;   // the three staged arrays
+    int rc = tmo::scratch_acquire(2 * tmo::align256(4 * M) + 8 * M, st, lease);
+    if (rc != TM_OK) {
+        cudaStreamDestroy(st);
+        return rc;
+    }
+    int32_t* ds = (int32_t*)lease.p;
+    int32_t* dd = (int32_t*)((char*)lease.p + tmo::align256(4 * M));
+    int64_t* dt = (int64_t*)((char*)lease.p + 2 * tmo::align256(4 * M));
+    cudaError_t e = cudaSuccess;
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(ds, src, 4 * (size_t)m, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(dd, dst, 4 * (size_t)m, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(dt, t, 8 * (size_t)m, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = tmo::cuda_status(e, "tm_graph_load copy", __FILE__, __LINE__);
     if (rc == TM_OK) rc = tmo::build_graph(ds, dd, dt, m, n_nodes, st, out);
-    cudaFreeAsync(ds, st);
-    cudaFreeAsync(dd, st);
-    cudaFreeAsync(dt, st);
+    tmo::scratch_release(lease, st);
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     return rc;

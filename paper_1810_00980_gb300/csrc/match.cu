@@ -1738,13 +1738,13 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         fail(cudaStreamSynchronize(st), "sync F");
     }
     const int64_t Fa = bounded ? F_ub : F;   // first edges the scratch holds
-    char* fb = nullptr;
+    ScratchLease fb;
     if (rc == TM_OK && Fa > 0) {
         size_t Fs = (size_t)Fa;
         size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
-        fail(cudaMallocAsync((void**)&fb, per_first_scratch_bytes(Fa, any_hoist), st), "per-edge scratch");
+        rc = scratch_acquire(per_first_scratch_bytes(Fa, any_hoist), st, fb);
         if (rc == TM_OK) {
-            char* q2 = fb;
+            char* q2 = (char*)fb.p;
             auto take2 = [&](size_t bytes) { char* r = q2; q2 += a256(bytes); return (void*)r; };
             int32_t* fwin = (int32_t*)take2(4 * Fs);
             int64_t* lo2 = (int64_t*)take2(8 * Fs);
@@ -1849,7 +1849,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                             pe.ms(ev_m1 >= 0 && ev_l1 >= 0 ? ev_m1 : ev_f1, ev_f1), wall, hW2, F,
                             ev_l0 >= 0 ? pe.ms(ev_w1, ev_l0) : 0.0, ev_l1 >= 0 ? pe.ms(ev_l2, ev_l1) : 0.0);
     }
-    if (fb) cudaFreeAsync(fb, st);
+    scratch_release(fb, st);
     cudaFreeAsync(sb, st);
     if (rc != TM_OK) return rc;
     if (dbg && dq_n > 0) {

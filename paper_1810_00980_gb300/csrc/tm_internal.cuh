@@ -298,7 +298,16 @@ int ensure_ex_tables(tm_graph* g, cudaStream_t st, bool need_own, bool need_rev,
 // per device; pool_free returns a stream-ordered block on an internal stream
 int pool_prepare(int dev);
 void pool_free(void* p, int dev);
-int pool_trim();
+int pool_trim();   // also frees the scratch arenas that no call holds
+// scratch of one call, leased from a per-device grow-only arena (slot >= 0) or, when every
+// arena is held, a pool block (slot < 0); usable on st from acquire to release
+struct ScratchLease {
+    void* p = nullptr;
+    int slot = -1;
+    int dev = 0;
+};
+int scratch_acquire(size_t bytes, cudaStream_t st, ScratchLease& L);
+void scratch_release(ScratchLease& L, cudaStream_t st);
 
 // profiling (abi.cu): phase events of the last batch / graph build, launch counter
 bool profiling();
