@@ -1215,121 +1215,149 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
     acc_flush_warp(acc, A.W.acc);
 }
 
-// per query: sums over its windows, per shift; Z_k and the mean (Algorithm 1)
-__global__ void __launch_bounds__(1024) k_fold(const QPlan* __restrict__ plans, WinDev W, tm_result* __restrict__ res,
-                       ShiftSums* __restrict__ sums, unsigned long long* __restrict__ subc) {
-    int qi = blockIdx.x;
+// Windows of one shift that a block of k_fold_shift sums: a query's shifts are cut into
+// fold_slices(J) slices of whole windows, a function of the query alone, so that its
+// result does not depend on the batch it runs in.
+constexpr int kFoldThreads = 256;
+constexpr int kFoldMaxSlices = 32;
+__host__ __device__ inline int fold_slices(int64_t nwin) {
+    int64_t s = (nwin + 8 * kFoldThreads - 1) / (8 * kFoldThreads);
+    return (int)(s < 1 ? 1 : (s > kFoldMaxSlices ? kFoldMaxSlices : s));
+}
+
+// Fold, first half: block (query, shift k, slice) sums the kept windows of its slice —
+// counts and work counters as integers, the Q64 weight sum W_j as a 128-bit integer, and
+// the doubles sum_j W_j / q_j (the shift's Z_k when q_j varies, Algorithm 1) and
+// sum_j W_j^2 (1 - q_j) / q_j^2 (Lemma 4.4) — into part[(sum_base + k) * smax + slice].
+__global__ void __launch_bounds__(kFoldThreads) k_fold_shift(const QPlan* __restrict__ plans, WinDev W,
+                                                             ShiftSums* __restrict__ part, int smax) {
+    const QPlan& Q = plans[blockIdx.x];
+    const int k = blockIdx.y, sl = blockIdx.z;
+    const int nsh = Q.l <= 0 ? 0 : (Q.mode == TM_MODE_EXACT ? 1 : Q.b);
+    const int64_t nwin = Q.mode == TM_MODE_EXACT ? 1 : Q.J;
+    const int ns = fold_slices(nwin);
+    if (k >= nsh || sl >= ns) return;
+    __shared__ ShiftSums sh[kFoldThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};   // count, first, cand, last, inst, kept
+    unsigned long long wlo = 0, whi = 0;
+    double zq = 0.0, vq = 0.0;
+    for (int64_t r = (int64_t)sl * kFoldThreads + threadIdx.x; r < nwin; r += (int64_t)ns * kFoldThreads) {
+        int64_t w = Q.win_base + (int64_t)k * nwin + r;
+        if (!W.kept[w]) continue;
+        const unsigned long long* a = W.acc + w * A_N;
+        c[0] += a[A_COUNT];
+        c[1] += a[A_FIRST];
+        c[2] += a[A_CAND];
+        c[3] += a[A_LAST];
+        c[4] += a[A_INST];
+        c[5] += 1;
+        unsigned long long x = wlo + a[A_WLO];
+        whi += a[A_WHI] + (x < wlo ? 1ull : 0ull);
+        wlo = x;
+        double y = (double)a[A_WHI] + (double)a[A_WLO] * 0x1.0p-64;
+        double qj = W.qj[w];
+        if (Q.q_mode == TM_Q_EDGES) zq += y / qj;
+        vq += y * y * (1.0 - qj) / (qj * qj);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) c[i] += __shfl_xor_sync(kFull, c[i], o);
+        unsigned long long l2 = __shfl_xor_sync(kFull, wlo, o);
+        unsigned long long h2 = __shfl_xor_sync(kFull, whi, o);
+        unsigned long long x = wlo + l2;
+        whi = whi + h2 + (x < wlo ? 1ull : 0ull);
+        wlo = x;
+        zq += __shfl_xor_sync(kFull, zq, o);
+        vq += __shfl_xor_sync(kFull, vq, o);
+    }
+    if (lane == 0) {
+        ShiftSums& o = sh[wid];
+        o.count = c[0]; o.first = c[1]; o.cand = c[2]; o.last = c[3]; o.inst = c[4]; o.kept = c[5];
+        o.wlo = wlo; o.whi = whi; o.zq = zq; o.vq = vq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ShiftSums t = sh[0];
+        for (int ww = 1; ww < kFoldThreads / 32; ww++) add_shift_sums(t, sh[ww]);
+        part[(Q.sum_base + k) * (int64_t)smax + sl] = t;
+    }
+}
+
+// Fold, second half: one thread per query adds its slices in order, then its shifts in
+// order: Z_k, their mean (the estimate of Algorithm 1), the mean variance estimate and
+// the spread of the Z_k (Welford).
+__global__ void k_fold_final(const QPlan* __restrict__ plans, int nq, WinDev W, const ShiftSums* __restrict__ part,
+                             int smax, tm_result* __restrict__ res, ShiftSums* __restrict__ sums,
+                             unsigned long long* __restrict__ subc) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= nq) return;
     const QPlan& Q = plans[qi];
-    __shared__ double sh_d[2][32];
-    __shared__ unsigned long long sh_u[A_N + 1][32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int64_t nwin = Q.mode == TM_MODE_EXACT ? 1 : Q.J;
-    int nsh = Q.mode == TM_MODE_EXACT ? 1 : Q.b;
-    if (Q.l <= 0) nsh = 0;   // query rejected on the host
-    double zsum = 0.0, vsum = 0.0, wmean = 0.0, wm2 = 0.0;   // Welford over the per-shift Z_k
-    unsigned long long tot[A_N + 1] = {0};   // + kept windows
+    const int nsh = Q.l <= 0 ? 0 : (Q.mode == TM_MODE_EXACT ? 1 : Q.b);
+    const int ns = fold_slices(Q.mode == TM_MODE_EXACT ? 1 : Q.J);
+    double zsum = 0.0, vsum = 0.0, wmean = 0.0, wm2 = 0.0;
+    ShiftSums tot = {};
     int overflow = 0;
     for (int k = 0; k < nsh; k++) {
-        unsigned long long s[A_N + 1] = {0};
-        double zq = 0.0, vq = 0.0;
-        unsigned long long wlo = 0, whi = 0;
-        for (int64_t r = threadIdx.x; r < nwin; r += blockDim.x) {
-            int64_t w = Q.win_base + (int64_t)k * nwin + r;
-            if (!W.kept[w]) continue;
-            const unsigned long long* a = W.acc + w * A_N;
-            s[A_COUNT] += a[A_COUNT];
-            for (int i = A_FIRST; i < A_N; i++) s[i] += a[i];
-            s[A_N] += 1;
-            unsigned long long x = wlo + a[A_WLO];
-            whi += a[A_WHI] + (x < wlo ? 1ull : 0ull);
-            wlo = x;
-            double y = (double)a[A_WHI] + (double)a[A_WLO] * 0x1.0p-64;
-            double qj = W.qj[w];
-            if (Q.q_mode == TM_Q_EDGES) zq += y / qj;
-            vq += y * y * (1.0 - qj) / (qj * qj);
-        }
-        // block reduce integer fields and the 128-bit weight
-        for (int o = 16; o > 0; o >>= 1) {
-            for (int i = 0; i <= A_N; i++)
-                if (i != A_WLO && i != A_WHI) s[i] += __shfl_xor_sync(kFull, s[i], o);
-            unsigned long long l2 = __shfl_xor_sync(kFull, wlo, o);
-            unsigned long long h2 = __shfl_xor_sync(kFull, whi, o);
-            unsigned long long x = wlo + l2;
-            whi = whi + h2 + (x < wlo ? 1ull : 0ull);
-            wlo = x;
-            zq += __shfl_xor_sync(kFull, zq, o);
-            vq += __shfl_xor_sync(kFull, vq, o);
-        }
-        s[A_WLO] = wlo;
-        s[A_WHI] = whi;
-        __syncthreads();
-        if (lane == 0) {
-            for (int i = 0; i <= A_N; i++) sh_u[i][wid] = s[i];
-            sh_d[0][wid] = zq;
-            sh_d[1][wid] = vq;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long u[A_N + 1] = {0};
-            double z2 = 0.0, v2 = 0.0;
-            unsigned long long L = 0, H = 0;
-            for (int ww = 0; ww < nw; ww++) {
-                for (int i = 0; i <= A_N; i++)
-                    if (i != A_WLO && i != A_WHI) u[i] += sh_u[i][ww];
-                unsigned long long x = L + sh_u[A_WLO][ww];
-                H += sh_u[A_WHI][ww] + (x < L ? 1ull : 0ull);
-                L = x;
-                z2 += sh_d[0][ww];
-                v2 += sh_d[1][ww];
-            }
-            if (sums) {
-                ShiftSums& o = sums[Q.sum_base + k];
-                o.count = u[A_COUNT]; o.wlo = L; o.whi = H; o.first = u[A_FIRST]; o.cand = u[A_CAND];
-                o.last = u[A_LAST]; o.inst = u[A_INST]; o.kept = u[A_N]; o.zq = z2; o.vq = v2;
-            }
-            if (H >= (1ull << 63) || u[A_COUNT] >= (1ull << 63)) overflow = 1;
-            for (int i = 0; i <= A_N; i++)
-                if (i != A_WLO && i != A_WHI) tot[i] += u[i];
-            double Wd = (double)H + (double)L * 0x1.0p-64;
-            double zk = Q.q_mode == TM_Q_EDGES ? z2 : Wd / Q.p;
-            zsum += zk;
-            vsum += v2;
-            double dz = zk - wmean;
-            wmean += dz / (k + 1);
-            wm2 += dz * (zk - wmean);
-        }
-        __syncthreads();
+        const ShiftSums* pk = part + (Q.sum_base + k) * (int64_t)smax;
+        ShiftSums u = pk[0];
+        for (int x = 1; x < ns; x++) add_shift_sums(u, pk[x]);
+        if (sums) sums[Q.sum_base + k] = u;
+        if (u.whi >= (1ull << 63) || u.count >= (1ull << 63)) overflow = 1;
+        add_shift_sums(tot, u);
+        double Wd = (double)u.whi + (double)u.wlo * 0x1.0p-64;
+        double zk = Q.q_mode == TM_Q_EDGES ? u.zq : Wd / Q.p;
+        zsum += zk;
+        vsum += u.vq;
+        double dz = zk - wmean;
+        wmean += dz / (k + 1);
+        wm2 += dz * (zk - wmean);
     }
-    if (threadIdx.x == 0 && subc) {
+    if (subc) {
         // counts of the exact queries at smaller spans (one window: the whole graph)
         const unsigned long long* a = W.acc + Q.win_base * A_N;
         for (int i = 0; i < kMaxSub; i++) subc[qi * kMaxSub + i] = (Q.l > 0 && i < Q.nsub) ? a[A_X0 + i] : 0;
     }
-    if (threadIdx.x == 0) {
-        tm_result r;
-        memset(&r, 0, sizeof(r));
-        r.status = Q.l <= 0 ? -1 : (overflow ? TM_EOVERFLOW : TM_OK);
-        r.count = (int64_t)tot[A_COUNT];
-        if (Q.mode == TM_MODE_EXACT) {
-            r.estimate = (double)tot[A_COUNT];
-            r.windows = 1;
-            r.windows_kept = 1;
-            r.var_hat = 0.0;
-            r.p_used = 1.0;
-        } else {
-            r.estimate = nsh ? zsum / nsh : 0.0;
-            r.windows = (int64_t)nsh * (Q.wclamp ? Q.J_all : Q.J);
-            r.windows_kept = Q.wclamp ? (int64_t)nsh * Q.J_all : (int64_t)tot[A_N];
-            r.var_hat = nsh ? vsum / nsh : 0.0;
-            r.shift_var = nsh >= 2 ? wm2 / (nsh - 1) : 0.0;
-            r.p_used = Q.p;
-        }
-        r.first_edges = (int64_t)tot[A_FIRST];
-        r.cand_edges = (int64_t)tot[A_CAND];
-        r.last_ranges = (int64_t)tot[A_LAST];
-        r.inst_read = (int64_t)tot[A_INST];
-        res[qi] = r;
+    tm_result r;
+    memset(&r, 0, sizeof(r));
+    r.status = Q.l <= 0 ? -1 : (overflow ? TM_EOVERFLOW : TM_OK);
+    r.count = (int64_t)tot.count;
+    if (Q.mode == TM_MODE_EXACT) {
+        r.estimate = (double)tot.count;
+        r.windows = 1;
+        r.windows_kept = 1;
+        r.var_hat = 0.0;
+        r.p_used = 1.0;
+    } else {
+        r.estimate = nsh ? zsum / nsh : 0.0;
+        r.windows = (int64_t)nsh * (Q.wclamp ? Q.J_all : Q.J);
+        r.windows_kept = Q.wclamp ? (int64_t)nsh * Q.J_all : (int64_t)tot.kept;
+        r.var_hat = nsh ? vsum / nsh : 0.0;
+        r.shift_var = nsh >= 2 ? wm2 / (nsh - 1) : 0.0;
+        r.p_used = Q.p;
     }
+    r.first_edges = (int64_t)tot.first;
+    r.cand_edges = (int64_t)tot.cand;
+    r.last_ranges = (int64_t)tot.last;
+    r.inst_read = (int64_t)tot.inst;
+    res[qi] = r;
+}
+
+// partial records per shift that the fold of these plans needs (smax per shift)
+int fold_smax(const std::vector<QPlan>& hp) {
+    int smax = 1;
+    for (const QPlan& P : hp)
+        if (P.l > 0 && P.mode != TM_MODE_EXACT) smax = std::max(smax, fold_slices(P.J));
+    return smax;
+}
+
+// both halves of the fold on st
+void launch_fold(const QPlan* dplans, int nq, int bmax, int smax, const WinDev& W, ShiftSums* part,
+                 tm_result* dres, ShiftSums* sums, unsigned long long* subc, cudaStream_t st) {
+    k_fold_shift<<<dim3((unsigned)nq, (unsigned)std::max(bmax, 1), (unsigned)smax), kFoldThreads, 0, st>>>(
+        dplans, W, part, smax);
+    k_fold_final<<<(unsigned)((nq + 63) / 64), 64, 0, st>>>(dplans, nq, W, part, smax, dres, sums, subc);
+    count_launch(2);
 }
 
 // ------------------------------------------------------- plain baseline K10
@@ -1629,12 +1657,16 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         }
     }
     // ---- scratch layout
+    const int smax = fold_smax(hp);
+    int bmax = 1;
+    for (const QPlan& P : hp) bmax = std::max(bmax, P.b);
     size_t NWs = (size_t)std::max<int64_t>(NW, 1);
     size_t Ms = (size_t)std::max<int64_t>(g->m, 1);
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
                 a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1)) +
+                a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax) +
                 a256(8 * kMaxSub * (size_t)nq);
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
@@ -1674,6 +1706,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     int64_t* dW2 = (int64_t*)take(8);
     unsigned long long* dctr = (unsigned long long*)take(8);
     ShiftSums* dsums = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
+    ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax);
     unsigned long long* dsubc = (unsigned long long*)take(8 * kMaxSub * (size_t)nq);
 
     int rc = TM_OK;
@@ -1800,9 +1833,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     if (rc == TM_OK) {
         int ev_f0 = pe.mark(st);
-        k_fold<<<nq, 1024, 0, st>>>(dplans, W, dres, dbg && dbg->sums ? dsums : nullptr,
-                                   dbg && dbg->sub_count ? dsubc : nullptr);
-        count_launch();
+        launch_fold(dplans, nq, bmax, smax, W, dpart, dres, dbg && dbg->sums ? dsums : nullptr,
+                    dbg && dbg->sub_count ? dsubc : nullptr, st);
         fail(cudaGetLastError(), "k_fold");
         ev_f1 = pe.mark(st);
         if (ev_m1 < 0) ev_m1 = ev_f0;
@@ -2243,7 +2275,8 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
     }
-    k_fold<<<1, 256, 0, st>>>(dplan, W, dres, nullptr, nullptr); count_launch();
+    // the scan workspace is free again: it holds the fold's one partial record
+    launch_fold(dplan, 1, 1, 1, W, (ShiftSums*)ws, dres, nullptr, nullptr, st);
     e = cudaGetLastError();
     tm_result hres;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st);
@@ -2314,8 +2347,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     b->nq = nq;
     b->qstat.assign((size_t)nq, TM_OK);
     std::vector<QPlan> hp((size_t)nq);
-    int64_t NW = 0, Fmax = 0;
-    int lmax = 1, kmax = 2;
+    int64_t NW = 0, Fmax = 0, n_sums = 0;
+    int lmax = 1, kmax = 2, bmax = 1;
     bool any_hoist = false;
     size_t wtab_bytes = 0;
     for (int i = 0; i < nq; i++) {
@@ -2338,6 +2371,9 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         P.full = 0;
         if (P.mode == TM_MODE_ESTIMATE) P.order = kOrdTime;
         P.win_base = NW;
+        P.sum_base = n_sums;
+        n_sums += P.mode == TM_MODE_EXACT ? 1 : P.b;
+        bmax = std::max(bmax, P.b);
         NW += P.mode == TM_MODE_EXACT ? 1 : P.J * P.b;
         Fmax += P.mode == TM_MODE_EXACT ? g->m : (int64_t)P.b * g->m;
         lmax = std::max(lmax, P.l);
@@ -2345,13 +2381,15 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         any_hoist |= P.hoist != 0 || P.ex23 != 0;
         if (P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) wtab_bytes += a256(16 * (size_t)(P.delta + 1));
     }
+    const int smax = fold_smax(hp);
     size_t NWs = (size_t)std::max<int64_t>(NW, 1), Fs = (size_t)std::max<int64_t>(Fmax, 1);
     int64_t ws1 = 2 * ((NW + 2047) / 2048) + 2;
     int64_t ws2 = scan_dn_ws_elems(Fmax) + 2;
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2) +
-                a256(4 * (Fs / 32 + 1)) + a256(8 * (Fs / 4 + 2)) + a256(4 * Fs);
+                a256(4 * (Fs / 32 + 1)) + a256(8 * (Fs / 4 + 2)) + a256(4 * Fs) +
+                a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax);
     cudaError_t e = cudaMalloc(&b->scratch, sz);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_res, sizeof(tm_result) * (size_t)nq);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -2398,6 +2436,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
     int32_t* bwin = (int32_t*)take(4 * nbw);
     int64_t* cf = (int64_t*)take(8 * ncf);
+    ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax);
 
     cudaStream_t st = b->cap;
     int rc = TM_OK;
@@ -2472,7 +2511,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         }
     }
     if (rc == TM_OK) {
-        k_fold<<<nq, 1024, 0, st>>>(dplans, W, dres, nullptr, nullptr); count_launch();
+        launch_fold(dplans, nq, bmax, smax, W, dpart, dres, nullptr, nullptr, st);
         fail(cudaGetLastError(), "k_fold");
     }
     fail(cudaMemcpyAsync(b->h_res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");

@@ -43,14 +43,6 @@ struct Seg {
     std::vector<int64_t> j_hi, own_hi;
 };
 
-void add_sums(ShiftSums& a, const ShiftSums& b) {
-    unsigned long long lo = a.wlo + b.wlo;
-    a.whi += b.whi + (lo < a.wlo ? 1ull : 0ull);
-    a.wlo = lo;
-    a.count += b.count; a.first += b.first; a.cand += b.cand; a.last += b.last;
-    a.inst += b.inst; a.kept += b.kept; a.zq += b.zq; a.vq += b.vq;
-}
-
 // the work of every live query inside edges [ea, eb); false if none can progress
 bool plan_segment(const int64_t* t, int64_t m, int64_t tmin, int64_t tmax, int64_t ea, int64_t eb,
                   std::vector<QState>& qs, Seg& sg) {
@@ -332,7 +324,7 @@ extern "C" int tm_stream_run(const int32_t* src, const int32_t* dst, const int64
             int64_t base = 0;
             for (size_t x = 0; x < k && rc == TM_OK; x++) {
                 QState& Q = qs[(size_t)cur.qidx[x]];
-                for (int kk = 0; kk < Q.b; kk++) add_sums(Q.acc[(size_t)kk], ssum[(size_t)(base + kk)]);
+                for (int kk = 0; kk < Q.b; kk++) add_shift_sums(Q.acc[(size_t)kk], ssum[(size_t)(base + kk)]);
                 base += Q.b;
             }
             tm_graph_free(g);

@@ -241,6 +241,14 @@ struct ShiftSums {
     unsigned long long count, wlo, whi, first, cand, last, inst, kept;
     double zq, vq;
 };
+// a += b (the weight sum as one 128-bit integer)
+__host__ __device__ inline void add_shift_sums(ShiftSums& a, const ShiftSums& b) {
+    unsigned long long lo = a.wlo + b.wlo;
+    a.whi += b.whi + (lo < a.wlo ? 1ull : 0ull);
+    a.wlo = lo;
+    a.count += b.count; a.first += b.first; a.cand += b.cand; a.last += b.last;
+    a.inst += b.inst; a.kept += b.kept; a.zq += b.zq; a.vq += b.vq;
+}
 
 struct BatchOut {                 // optional per-window readback for one query
     int query = -1;
