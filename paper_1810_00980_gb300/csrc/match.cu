@@ -379,9 +379,16 @@ __device__ __forceinline__ void add_sub_range(Acc& a, const QPlan& Q, const TT* 
 // first edge at t1 and last edge at t3 counts for rider R's shift k when the window of t1 is
 // kept and holds t3, and t3 - t1 <= R.delta; it adds R's Q64 weight to that window's sums.
 // Out of line: rare next to the enumeration, and it keeps the matcher's registers.
+// x / d for x >= 0, d > 0: one 32-bit division when both fit in 32 bits (times of a graph
+// whose span fits in 31 bits, and spans c delta below 2^32), else the 64-bit one
+__device__ __forceinline__ int64_t div_nonneg(int64_t x, int64_t d) {
+    if ((((unsigned long long)x | (unsigned long long)d) >> 32) == 0) return (int64_t)((uint32_t)x / (uint32_t)d);
+    return x / d;
+}
+
 __device__ __forceinline__ void ride_window(const QPlan& R, int k, int64_t t1, int64_t& w, int64_t& thi) {
-    int64_t s = -(int64_t)(draw(R.seed, (uint64_t)k, 0) % (uint64_t)R.cd) - R.t_off;
-    int64_t j = (t1 - s) / R.cd;   // 0-based window of t1
+    int64_t s = __ldg(R.shifts + k);
+    int64_t j = div_nonneg(t1 - s, R.cd);   // 0-based window of t1
     w = R.win_base + (int64_t)k * R.J + j;
     thi = min(t1 + R.delta, s + (j + 1) * R.cd - 1);
 }
@@ -606,7 +613,7 @@ __device__ __forceinline__ int64_t first_thi(const QPlan& Q, const WinDev& W, in
     int64_t tend = W.tend[win];
     if (Q.wclamp) {
         int64_t s = W.start[win];
-        tend = s + ((t1 - s) / Q.cd + 1) * Q.cd - 1;
+        tend = s + (div_nonneg(t1 - s, Q.cd) + 1) * Q.cd - 1;
     }
     return min(t1 + Q.delta, tend);
 }
@@ -1656,6 +1663,12 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                           a256(8 * (size_t)hp[(size_t)i].b * (size_t)(hp[(size_t)i].J + 1));
         }
     }
+    // window origins of the riding estimates' shifts, read per instance on the device
+    std::vector<int64_t> h_shifts;
+    for (const QPlan& P : hp)
+        if (P.riding)
+            for (int k = 0; k < P.b; k++)
+                h_shifts.push_back(-(int64_t)(draw(P.seed, (uint64_t)k, 0) % (uint64_t)P.cd) - P.t_off);
     // ---- scratch layout
     const int smax = fold_smax(hp);
     int bmax = 1;
@@ -1667,7 +1680,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
                 a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1)) +
                 a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax) +
-                a256(8 * kMaxSub * (size_t)nq);
+                a256(8 * kMaxSub * (size_t)nq) + a256(8 * std::max<size_t>(h_shifts.size(), 1));
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
     char* p = sb;
@@ -1708,6 +1721,12 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     ShiftSums* dsums = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
     ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax);
     unsigned long long* dsubc = (unsigned long long*)take(8 * kMaxSub * (size_t)nq);
+    int64_t* dshifts = (int64_t*)take(8 * std::max<size_t>(h_shifts.size(), 1));
+    for (size_t i = 0, o = 0; i < (size_t)nq; i++)
+        if (hp[i].riding) {
+            hp[i].shifts = dshifts + o;
+            o += (size_t)hp[i].b;
+        }
 
     int rc = TM_OK;
     auto fail = [&](cudaError_t e, const char* what) {
@@ -1718,6 +1737,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     int ev_w0 = pe.mark(st), ev_w1 = -1, ev_l0 = -1, ev_l1 = -1, ev_l2 = -1, ev_m1 = -1, ev_f1 = -1;
     int64_t hW2 = 0;
     fail(cudaMemcpyAsync(dplans, hp.data(), sizeof(QPlan) * (size_t)nq, cudaMemcpyHostToDevice, st), "plans");
+    if (!h_shifts.empty())
+        fail(cudaMemcpyAsync(dshifts, h_shifts.data(), 8 * h_shifts.size(), cudaMemcpyHostToDevice, st), "shifts");
     fail(cudaMemsetAsync(W.acc, 0, 8 * A_N * NWs, st), "acc");
     fail(cudaMemsetAsync(dctr, 0, 8, st), "counter");
     for (int i = 0; i < nq && rc == TM_OK; i++) {

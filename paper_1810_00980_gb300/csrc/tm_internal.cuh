@@ -215,6 +215,7 @@ struct QPlan {
     int32_t nride;
     int32_t riding;      // 1: this estimate rides along with an exact query (no first edges)
     int32_t ride_q[6];   // plan indices of the riders
+    const int64_t* shifts;   // riding estimates: [b] window origins -(shift draw mod cd) - t_off
     LevelPlan lv[TM_L_MAX];
 };
 constexpr int kMaxSub = 3;
