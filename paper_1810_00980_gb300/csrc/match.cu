@@ -347,8 +347,9 @@ __device__ __forceinline__ void q64_weight(int64_t cd, int64_t dur, unsigned lon
 __device__ __forceinline__ void add_weight(Acc& a, const QPlan& Q, int64_t dur) {
     unsigned long long wi, wf;
     if (Q.wtab) {
-        wi = __ldg(Q.wtab + 2 * dur);
-        wf = __ldg(Q.wtab + 2 * dur + 1);
+        const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(Q.wtab) + dur);   // one 16-byte load
+        wi = e.x;
+        wf = e.y;
     } else {
         q64_weight(Q.cd, dur, wi, wf);
     }
@@ -405,8 +406,9 @@ __device__ __forceinline__ void ride_weight(const QPlan& R, int64_t dur, unsigne
                                             unsigned long long& lo, unsigned long long& hi) {
     unsigned long long wi, wf;
     if (R.wtab) {
-        wi = __ldg(R.wtab + 2 * dur);
-        wf = __ldg(R.wtab + 2 * dur + 1);
+        const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(R.wtab) + dur);   // one 16-byte load
+        wi = e.x;
+        wf = e.y;
     } else {
         q64_weight(R.cd, dur, wi, wf);
     }
@@ -464,8 +466,9 @@ __device__ __noinline__ void ride_range(const QPlan* __restrict__ PL, const QPla
 __device__ __forceinline__ void add_weight_n(Acc& a, const QPlan& Q, int64_t dur, unsigned long long n) {
     unsigned long long wi, wf;
     if (Q.wtab) {
-        wi = __ldg(Q.wtab + 2 * dur);
-        wf = __ldg(Q.wtab + 2 * dur + 1);
+        const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(Q.wtab) + dur);   // one 16-byte load
+        wi = e.x;
+        wf = e.y;
     } else {
         q64_weight(Q.cd, dur, wi, wf);
     }
