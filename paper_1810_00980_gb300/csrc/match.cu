@@ -15,8 +15,10 @@
 //              expanded warp-cooperatively (range lengths scanned across the
 //              warp, each lane takes one candidate, owner found by shuffles);
 //              in exact mode the last motif edge is counted by range length.
-//   k_fold     per query: Z_k = sum_j W_j / q_j per shift and the mean over
-//              shifts (Algorithm 1's return value).
+//   k_fold_shift, k_fold_final
+//              per query, shift and slice of windows the partial sums, then per
+//              query: Z_k = sum_j W_j / q_j per shift and the mean over shifts
+//              (Algorithm 1's return value).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -1859,7 +1861,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         int ev_f0 = pe.mark(st);
         launch_fold(dplans, nq, bmax, smax, W, dpart, dres, dbg && dbg->sums ? dsums : nullptr,
                     dbg && dbg->sub_count ? dsubc : nullptr, st);
-        fail(cudaGetLastError(), "k_fold");
+        fail(cudaGetLastError(), "fold");
         ev_f1 = pe.mark(st);
         if (ev_m1 < 0) ev_m1 = ev_f0;
     }
@@ -2536,7 +2538,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     }
     if (rc == TM_OK) {
         launch_fold(dplans, nq, bmax, smax, W, dpart, dres, nullptr, nullptr, st);
-        fail(cudaGetLastError(), "k_fold");
+        fail(cudaGetLastError(), "fold");
     }
     fail(cudaMemcpyAsync(b->h_res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
     cudaGraph_t graph = nullptr;

@@ -341,7 +341,7 @@ extern "C" int tm_stream_run(const int32_t* src, const int32_t* dst, const int64
         slot ^= 1;
     }
 
-    // results, folded as k_fold folds one batch
+    // results, folded as the fold kernels fold one batch
     if (rc == TM_OK) {
         for (int i = 0; i < n_queries; i++) {
             if (results[i].status != TM_OK) continue;
