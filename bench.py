@@ -803,6 +803,7 @@ def main():
         "rel_err": rel_err, "rel_err_max": max(rel_err.values()) if rel_err else None,
         "plain_exact_queries_per_s": plain_qps,
         "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
+        "match_ms_per_step": [round(x, 3) for x in match_ms],
         "phases_ms": {k: p_last.get(k) for k in ("graph_ms", "windows_ms", "level2_ms", "match_ms", "fold_ms")},
         "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
