@@ -129,11 +129,14 @@ class ClockSampler:
             if self.thread:
                 self.thread.join(timeout=2)
 
-    def summary(self, t0=None, t1=None):
-        """Samples taken between host times t0 and t1 (the timed region), else all."""
+    def summary(self, t0=None, t1=None, slack=0.15):
+        """Samples taken between host times t0 and t1 (the timed region); when a short region
+        holds none, those from slack seconds before it (the warm-up steps, under load); else all."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         inside = [ln for (ts, ln) in self.lines if t0 is not None and t0 <= ts <= t1]
+        if not inside and t0 is not None:
+            inside = [ln for (ts, ln) in self.lines if t0 - slack <= ts <= t1]
         for ln in (inside or [ln for _, ln in self.lines]):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
@@ -638,18 +641,22 @@ def main():
             g.free()
         return b
 
-    for _ in range(args.warmup):
-        batch = step_device()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches0 = tm.profile_last()["launches"]
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     match_ms, level2_ms, prof = [], [], []
     step_ms = []
+    # the clock sampler starts first, so that its start-up (NVML initialisation, about a
+    # second with the device idle) is over before the warm-up; the warm-up runs W steps and
+    # at least 0.3 s, so that the samples just before a short timed region are under load
     with ClockSampler(torch.cuda.current_device()) as clk:
+        warm_run, w_t0 = 0, time.time()
+        while warm_run < args.warmup or time.time() - w_t0 < 0.3:
+            batch = step_device()
+            warm_run += 1
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches0 = tm.profile_last()["launches"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         clk_t0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
@@ -803,7 +810,7 @@ def main():
         "rel_err": rel_err, "rel_err_max": max(rel_err.values()) if rel_err else None,
         "plain_exact_queries_per_s": plain_qps,
         "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
-        "match_ms_per_step": [round(x, 3) for x in match_ms],
+        "match_ms_per_step": [round(x, 3) for x in match_ms], "warmup_steps_run": warm_run,
         "phases_ms": {k: p_last.get(k) for k in ("graph_ms", "windows_ms", "level2_ms", "match_ms", "fold_ms")},
         "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
