@@ -301,3 +301,85 @@ def test_estimate_p1_small_c_edge_cases(oracle_mod):
         assert z == pytest.approx(sum(r["W"] for r in recs), rel=1e-13)
     e = np.zeros(0, np.int32)
     assert oracle_mod.estimate(e, e, np.zeros(0, np.int64), *motif, 7, 3, 0.5, seed=1) == 0.0
+
+
+# ---------------------------------------------------------------- P4 through the oracle's own steps
+def _seed_for_shift(orng, cd, s, k=0):
+    """The first seed whose repetition-k shift is s (shift draws are pinned by the
+    SplitMix64 known answers; this only searches them)."""
+    seed = 0
+    while orng.shift(seed, k, cd) != s:
+        seed += 1
+    return seed
+
+
+def test_window_weights_hand_worked(oracle_mod):
+    """Windows of Eq. 1 and their weights W_j (Eqs. 2-3) on a hand-worked graph,
+    through window_records, z_from_records and estimate: an edge on a window's
+    last tick a_j + c delta - 1 belongs to the window, an instance straddling a
+    boundary belongs to none, and each instance adds c delta / (c delta - Delta)."""
+    from fractions import Fraction
+    g = json.load(open(os.path.join(GOLDEN, "window_weights.json")))
+    src, dst, t = _arr(g["edges"])
+    mu = [e[0] for e in g["motif"]]
+    mv = [e[1] for e in g["motif"]]
+    delta, c = g["delta"], g["c"]
+    cd = c * delta
+    cnt, hist, _ = oracle_mod.count_exact_hist(src, dst, t, mu, mv, delta)
+    assert cnt == g["count"]
+    assert {d: int(x) for d, x in enumerate(hist) if x} == {int(k): v for k, v in g["hist"].items()}
+    for sh in g["shifts"]:
+        seed = _seed_for_shift(oracle_mod.rng, cd, sh["s"])
+        s, recs = oracle_mod.window_records(src, dst, t, mu, mv, delta, c, seed, p=1.0)
+        assert s == sh["s"]
+        assert len(recs) == len(sh["windows"])
+        for r, w in zip(recs, sh["windows"]):
+            assert (r["j"], r["a"], r["end"], r["lo"], r["hi"], r["count"]) == \
+                (w["j"], w["start"], w["end"], w["lo"], w["hi"], w["count"])
+            # each term is rounded once to fp64, then summed: within a few ulp of the fraction
+            assert r["W"] == pytest.approx(float(Fraction(*w["W"])), rel=1e-14, abs=0.0)
+        want1 = float(sum(Fraction(*w["W"]) for w in sh["windows"]))
+        assert oracle_mod.estimate(src, dst, t, mu, mv, delta, c, 1.0, seed) == pytest.approx(want1, rel=1e-14, abs=0.0)
+        # p = 1/2: Z = sum over kept windows of W_j / q_j (Algorithm 1's combination step)
+        p = 0.5
+        kept = [oracle_mod.rng.uniform(seed, 0, w["j"]) < p for w in sh["windows"]]
+        want = float(sum(Fraction(*w["W"]) / Fraction(1, 2) for w, k in zip(sh["windows"], kept) if k))
+        assert oracle_mod.estimate(src, dst, t, mu, mv, delta, c, p, seed) == pytest.approx(want, rel=1e-14, abs=0.0)
+        # Algorithm 1 first normalises times to start at 0: translating every timestamp
+        # changes no window, count or weight
+        s2, recs2 = oracle_mod.window_records(src, dst, t + 1_000_003, mu, mv, delta, c, seed, p=1.0)
+        assert s2 == s
+        assert [(r["j"], r["a"], r["lo"], r["hi"], r["count"], r["W"]) for r in recs2] == \
+            [(r["j"], r["a"], r["lo"], r["hi"], r["count"], r["W"]) for r in recs]
+
+
+@pytest.mark.parametrize("motif,delta", [(([0, 1, 2], [1, 2, 0]), 9), (([0, 1, 0], [1, 0, 1]), 7),
+                                         (([2, 2, 2], [0, 1, 0]), 8)])
+def test_lemma41_through_window_records_and_estimate(oracle_mod, motif, delta):
+    """Lemma 4.1 driven through the oracle's own Algorithm 1 steps: with every
+    window kept (p = 1), summed over all c delta shifts s, (i) the per-window
+    duration histograms of window_records give (c delta - Delta) H[Delta]
+    exactly (Eq. 2: an instance of duration Delta lies inside a window for
+    c delta - Delta shifts), and (ii) the weights sum_j W_j, and the estimates
+    themselves, add up to c delta C_M (to 1e-12), i.e. the mean over shifts of
+    ||Y_s||_1 is C_M."""
+    rng = np.random.default_rng(4100 + delta)
+    src, dst, t = synth.random_small_graph(rng, 4, 200, 300)
+    for c in (2, 3):
+        cd = c * delta
+        C, H, _ = oracle_mod.count_exact_hist(src, dst, t, *motif, delta)
+        assert C > 0
+        tot = np.zeros(delta + 1, np.int64)
+        w_sums, z_sums = [], []
+        for s in range(-cd + 1, 1):
+            seed = _seed_for_shift(oracle_mod.rng, cd, s)
+            s_got, recs = oracle_mod.window_records(src, dst, t, *motif, delta, c, seed, p=1.0)
+            assert s_got == s
+            for r in recs:
+                if r["count"]:
+                    tot += r["hist"]
+            w_sums.append(math.fsum(r["W"] for r in recs))
+            z_sums.append(oracle_mod.estimate(src, dst, t, *motif, delta, c, 1.0, seed))
+        assert np.array_equal(tot, np.array([(cd - d) * H[d] for d in range(delta + 1)]))
+        assert abs(math.fsum(w_sums) - cd * C) <= 1e-12 * cd * C
+        assert abs(math.fsum(z_sums) - cd * C) <= 1e-12 * cd * C
