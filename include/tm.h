@@ -208,7 +208,8 @@ int tm_run_batch(const tm_graph* g, const tm_query* queries, int32_t n_queries,
  * static device array compiled into the library, TM_NOALLOC_SCRATCH_BYTES
  * (about 7.4 MB) on every GPU that loads the library, held until the process
  * exits.
- *   g       graph with at most TM_NOALLOC_MAX_EDGES edges (else TM_EINVAL).
+ *   g       graph with at most TM_NOALLOC_MAX_EDGES edges (else TM_EINVAL), loaded on
+ *           the current device (else TM_EINVAL: the array used is the current device's).
  *   stream  cudaStream_t as void* (NULL: legacy default stream); the work is
  *           ordered on it and the call returns once *count is on the host.
  *   count   host pointer receiving C_M.

@@ -1240,59 +1240,64 @@ __host__ __device__ inline int fold_slices(int64_t nwin) {
 // Fold, first half: block (query, shift k, slice) sums the kept windows of its slice —
 // counts and work counters as integers, the Q64 weight sum W_j as a 128-bit integer, and
 // the doubles sum_j W_j / q_j (the shift's Z_k when q_j varies, Algorithm 1) and
-// sum_j W_j^2 (1 - q_j) / q_j^2 (Lemma 4.4) — into part[(sum_base + k) * smax + slice].
+// sum_j W_j^2 (1 - q_j) / q_j^2 (Lemma 4.4) — into part[part_base + k * slices + slice].
+// The grid's y extent is capped at the hardware limit; a block then also takes the shifts
+// k + gridDim.y, k + 2 gridDim.y, ... (a loop that is uniform across the block).
 __global__ void __launch_bounds__(kFoldThreads) k_fold_shift(const QPlan* __restrict__ plans, WinDev W,
-                                                             ShiftSums* __restrict__ part, int smax) {
+                                                             ShiftSums* __restrict__ part) {
     const QPlan& Q = plans[blockIdx.x];
-    const int k = blockIdx.y, sl = blockIdx.z;
+    const int sl = blockIdx.z;
     const int nsh = Q.l <= 0 ? 0 : (Q.mode == TM_MODE_EXACT ? 1 : Q.b);
     const int64_t nwin = Q.mode == TM_MODE_EXACT ? 1 : Q.J;
     const int ns = fold_slices(nwin);
-    if (k >= nsh || sl >= ns) return;
+    if (sl >= ns) return;
     __shared__ ShiftSums sh[kFoldThreads / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};   // count, first, cand, last, inst, kept
-    unsigned long long wlo = 0, whi = 0;
-    double zq = 0.0, vq = 0.0;
-    for (int64_t r = (int64_t)sl * kFoldThreads + threadIdx.x; r < nwin; r += (int64_t)ns * kFoldThreads) {
-        int64_t w = Q.win_base + (int64_t)k * nwin + r;
-        if (!W.kept[w]) continue;
-        const unsigned long long* a = W.acc + w * A_N;
-        c[0] += a[A_COUNT];
-        c[1] += a[A_FIRST];
-        c[2] += a[A_CAND];
-        c[3] += a[A_LAST];
-        c[4] += a[A_INST];
-        c[5] += 1;
-        unsigned long long x = wlo + a[A_WLO];
-        whi += a[A_WHI] + (x < wlo ? 1ull : 0ull);
-        wlo = x;
-        double y = (double)a[A_WHI] + (double)a[A_WLO] * 0x1.0p-64;
-        double qj = W.qj[w];
-        if (Q.q_mode == TM_Q_EDGES) zq += y / qj;
-        vq += y * y * (1.0 - qj) / (qj * qj);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int k = blockIdx.y; k < nsh; k += gridDim.y) {
+        unsigned long long c[6] = {0, 0, 0, 0, 0, 0};   // count, first, cand, last, inst, kept
+        unsigned long long wlo = 0, whi = 0;
+        double zq = 0.0, vq = 0.0;
+        for (int64_t r = (int64_t)sl * kFoldThreads + threadIdx.x; r < nwin; r += (int64_t)ns * kFoldThreads) {
+            int64_t w = Q.win_base + (int64_t)k * nwin + r;
+            if (!W.kept[w]) continue;
+            const unsigned long long* a = W.acc + w * A_N;
+            c[0] += a[A_COUNT];
+            c[1] += a[A_FIRST];
+            c[2] += a[A_CAND];
+            c[3] += a[A_LAST];
+            c[4] += a[A_INST];
+            c[5] += 1;
+            unsigned long long x = wlo + a[A_WLO];
+            whi += a[A_WHI] + (x < wlo ? 1ull : 0ull);
+            wlo = x;
+            double y = (double)a[A_WHI] + (double)a[A_WLO] * 0x1.0p-64;
+            double qj = W.qj[w];
+            if (Q.q_mode == TM_Q_EDGES) zq += y / qj;
+            vq += y * y * (1.0 - qj) / (qj * qj);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int i = 0; i < 6; i++) c[i] += __shfl_xor_sync(kFull, c[i], o);
-        unsigned long long l2 = __shfl_xor_sync(kFull, wlo, o);
-        unsigned long long h2 = __shfl_xor_sync(kFull, whi, o);
-        unsigned long long x = wlo + l2;
-        whi = whi + h2 + (x < wlo ? 1ull : 0ull);
-        wlo = x;
-        zq += __shfl_xor_sync(kFull, zq, o);
-        vq += __shfl_xor_sync(kFull, vq, o);
-    }
-    if (lane == 0) {
-        ShiftSums& o = sh[wid];
-        o.count = c[0]; o.first = c[1]; o.cand = c[2]; o.last = c[3]; o.inst = c[4]; o.kept = c[5];
-        o.wlo = wlo; o.whi = whi; o.zq = zq; o.vq = vq;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ShiftSums t = sh[0];
-        for (int ww = 1; ww < kFoldThreads / 32; ww++) add_shift_sums(t, sh[ww]);
-        part[(Q.sum_base + k) * (int64_t)smax + sl] = t;
+            for (int i = 0; i < 6; i++) c[i] += __shfl_xor_sync(kFull, c[i], o);
+            unsigned long long l2 = __shfl_xor_sync(kFull, wlo, o);
+            unsigned long long h2 = __shfl_xor_sync(kFull, whi, o);
+            unsigned long long x = wlo + l2;
+            whi = whi + h2 + (x < wlo ? 1ull : 0ull);
+            wlo = x;
+            zq += __shfl_xor_sync(kFull, zq, o);
+            vq += __shfl_xor_sync(kFull, vq, o);
+        }
+        if (lane == 0) {
+            ShiftSums& o = sh[wid];
+            o.count = c[0]; o.first = c[1]; o.cand = c[2]; o.last = c[3]; o.inst = c[4]; o.kept = c[5];
+            o.wlo = wlo; o.whi = whi; o.zq = zq; o.vq = vq;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ShiftSums t = sh[0];
+            for (int ww = 1; ww < kFoldThreads / 32; ww++) add_shift_sums(t, sh[ww]);
+            part[Q.part_base + (int64_t)k * ns + sl] = t;
+        }
+        __syncthreads();   // sh is written again by the next shift
     }
 }
 
@@ -1300,7 +1305,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_fold_shift(const QPlan* __rest
 // order: Z_k, their mean (the estimate of Algorithm 1), the mean variance estimate and
 // the spread of the Z_k (Welford).
 __global__ void k_fold_final(const QPlan* __restrict__ plans, int nq, WinDev W, const ShiftSums* __restrict__ part,
-                             int smax, tm_result* __restrict__ res, ShiftSums* __restrict__ sums,
+                             tm_result* __restrict__ res, ShiftSums* __restrict__ sums,
                              unsigned long long* __restrict__ subc) {
     int qi = blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= nq) return;
@@ -1311,7 +1316,7 @@ __global__ void k_fold_final(const QPlan* __restrict__ plans, int nq, WinDev W, 
     ShiftSums tot = {};
     int overflow = 0;
     for (int k = 0; k < nsh; k++) {
-        const ShiftSums* pk = part + (Q.sum_base + k) * (int64_t)smax;
+        const ShiftSums* pk = part + Q.part_base + (int64_t)k * ns;
         ShiftSums u = pk[0];
         for (int x = 1; x < ns; x++) add_shift_sums(u, pk[x]);
         if (sums) sums[Q.sum_base + k] = u;
@@ -1355,21 +1360,46 @@ __global__ void k_fold_final(const QPlan* __restrict__ plans, int nq, WinDev W, 
     res[qi] = r;
 }
 
-// partial records per shift that the fold of these plans needs (smax per shift)
-int fold_smax(const std::vector<QPlan>& hp) {
-    int smax = 1;
-    for (const QPlan& P : hp)
-        if (P.l > 0 && P.mode != TM_MODE_EXACT) smax = std::max(smax, fold_slices(P.J));
-    return smax;
+// the fold's partial records: part_base of every plan (a query's shifts times its slices,
+// one after another); returns the total and, through smax, the most slices of a query
+int64_t fold_parts(std::vector<QPlan>& hp, int& smax) {
+    int64_t n = 0;
+    smax = 1;
+    for (QPlan& P : hp) {
+        P.part_base = n;
+        if (P.l <= 0) continue;
+        int ns = fold_slices(P.mode == TM_MODE_EXACT ? 1 : P.J);
+        smax = std::max(smax, ns);
+        n += (int64_t)(P.mode == TM_MODE_EXACT ? 1 : P.b) * ns;
+    }
+    return std::max<int64_t>(n, 1);
 }
+
+constexpr int kMaxGridY = 65535;
 
 // both halves of the fold on st
 void launch_fold(const QPlan* dplans, int nq, int bmax, int smax, const WinDev& W, ShiftSums* part,
                  tm_result* dres, ShiftSums* sums, unsigned long long* subc, cudaStream_t st) {
-    k_fold_shift<<<dim3((unsigned)nq, (unsigned)std::max(bmax, 1), (unsigned)smax), kFoldThreads, 0, st>>>(
-        dplans, W, part, smax);
-    k_fold_final<<<(unsigned)((nq + 63) / 64), 64, 0, st>>>(dplans, nq, W, part, smax, dres, sums, subc);
+    unsigned gy = (unsigned)std::min(std::max(bmax, 1), kMaxGridY);
+    k_fold_shift<<<dim3((unsigned)nq, gy, (unsigned)smax), kFoldThreads, 0, st>>>(dplans, W, part);
+    k_fold_final<<<(unsigned)((nq + 63) / 64), 64, 0, st>>>(dplans, nq, W, part, dres, sums, subc);
     count_launch(2);
+}
+
+// the persistent matcher for a batch whose deepest motif has lmax edges on kmax nodes: the
+// instantiation whose register budget fits the tuning's blocks per SM
+template <typename TT>
+void launch_match(const MatchArgs<TT>& A, int lmax, int kmax, const Tuning& tu, int nsm, cudaStream_t st) {
+    const int bps = tu.blocks_per_sm, bt = tu.block_threads;
+    const unsigned gm = (unsigned)(nsm * bps);
+    const size_t sm = match_smem_bytes(A.nq, bt);
+    if (lmax <= 3 && kmax <= 4 && bps >= 6) k_match<TT, 3, 4, 6><<<gm, bt, sm, st>>>(A);
+    else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, sm, st>>>(A);
+    else if (lmax <= 4 && kmax <= 4 && bps >= 4) k_match<TT, 4, 4, 4><<<gm, bt, sm, st>>>(A);
+    else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, sm, st>>>(A);
+    else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, sm, st>>>(A);
+    else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, sm, st>>>(A);
+    count_launch();
 }
 
 // ------------------------------------------------------- plain baseline K10
@@ -1675,7 +1705,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             for (int k = 0; k < P.b; k++)
                 h_shifts.push_back(-(int64_t)(draw(P.seed, (uint64_t)k, 0) % (uint64_t)P.cd) - P.t_off);
     // ---- scratch layout
-    const int smax = fold_smax(hp);
+    int smax = 1;
+    const int64_t n_parts = fold_parts(hp, smax);
     int bmax = 1;
     for (const QPlan& P : hp) bmax = std::max(bmax, P.b);
     size_t NWs = (size_t)std::max<int64_t>(NW, 1);
@@ -1684,7 +1715,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
                 a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1)) +
-                a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax) +
+                a256(sizeof(ShiftSums) * (size_t)n_parts) +
                 a256(8 * kMaxSub * (size_t)nq) + a256(8 * std::max<size_t>(h_shifts.size(), 1));
     char* sb = nullptr;
     TM_CUDA(cudaMallocAsync((void**)&sb, sz, st));
@@ -1724,7 +1755,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     int64_t* dW2 = (int64_t*)take(8);
     unsigned long long* dctr = (unsigned long long*)take(8);
     ShiftSums* dsums = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
-    ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax);
+    ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)n_parts);
     unsigned long long* dsubc = (unsigned long long*)take(8 * kMaxSub * (size_t)nq);
     int64_t* dshifts = (int64_t*)take(8 * std::max<size_t>(h_shifts.size(), 1));
     for (size_t i = 0, o = 0; i < (size_t)nq; i++)
@@ -1821,7 +1852,6 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             A.enum_threshold = tu.enum_threshold;
             A.chunk = tu.chunk_items;
             A.blockwin = bwin; A.chunkf = cf; A.nchunkf = (int64_t)ncf;
-            int bt = tu.block_threads;
             int64_t gl2 = std::min<int64_t>((Fa + 255) / 256, (int64_t)nsm * 8);
             k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
                 W.fbase, NW, Fa, d_Fk, bwin);
@@ -1839,17 +1869,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             }
             ev_l1 = pe.mark(st);
             if (rc == TM_OK) {
-                int bps = tu.blocks_per_sm;
-                unsigned gm = (unsigned)(nsm * bps);
-                if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
-                    k_match<TT, 3, 4, 6><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-                else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-                else if (lmax <= 4 && kmax <= 4 && tu.blocks_per_sm >= 4)
-                    k_match<TT, 4, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-                else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-                else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-                else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-                count_launch();
+                launch_match<TT>(A, lmax, kmax, tu, nsm, st);
                 fail(cudaGetLastError(), "k_match");
                 ev_m1 = pe.mark(st);
                 if (pe.on) fail(cudaMemcpyAsync(&hW2, dW2, 8, cudaMemcpyDeviceToHost, st), "W2");
@@ -2223,6 +2243,12 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
     unsigned char* base = nullptr;
     int rc = na_scratch(&base);
     if (rc != TM_OK) return rc;
+    // the array is resolved for the current device, and the kernels run there: the graph
+    // must live on that device too
+    int cur = -1;
+    cudaError_t ce = cudaGetDevice(&cur);
+    if (ce != cudaSuccess) return na_status(ce);
+    if (cur != g->device) return TM_EINVAL;
     unsigned char* p = base;
     auto take = [&](size_t bytes) { unsigned char* r = p; p += na_a256(bytes); return (void*)r; };
     QPlan* dplan = (QPlan*)take(sizeof(QPlan));
@@ -2292,12 +2318,7 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         // workspace takes the second half
         rc = scan_lengths((const int32_t*)len2, excl, F, nullptr, dW2, len2 + kNaMaxEdges / 2, kNaMaxEdges / 2, st);
         if (rc != TM_OK) return rc;
-        unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
-        if (P.l <= 3 && P.k <= 4) k_match<TT, 3, 4><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
-        else if (P.l <= 4 && P.k <= 4) k_match<TT, 4, 4><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
-        else if (P.l <= 4) k_match<TT, 4, TM_K_MAX><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
-        else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, tu.block_threads, match_smem_bytes(A.nq, tu.block_threads), st>>>(A);
-        count_launch();
+        launch_match<TT>(A, P.l, std::max(P.k, 2), tu, nsm, st);
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
     }
@@ -2407,7 +2428,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         any_hoist |= P.hoist != 0 || P.ex23 != 0;
         if (P.mode == TM_MODE_ESTIMATE && P.delta + 1 <= kWtabMax) wtab_bytes += a256(16 * (size_t)(P.delta + 1));
     }
-    const int smax = fold_smax(hp);
+    int smax = 1;
+    const int64_t n_parts = fold_parts(hp, smax);
     size_t NWs = (size_t)std::max<int64_t>(NW, 1), Fs = (size_t)std::max<int64_t>(Fmax, 1);
     int64_t ws1 = 2 * ((NW + 2047) / 2048) + 2;
     int64_t ws2 = scan_dn_ws_elems(Fmax) + 2;
@@ -2415,7 +2437,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
                 a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2) +
                 a256(4 * (Fs / 32 + 1)) + a256(8 * (Fs / 4 + 2)) + a256(4 * Fs) +
-                a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax);
+                a256(sizeof(ShiftSums) * (size_t)n_parts);
     cudaError_t e = cudaMalloc(&b->scratch, sz);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_res, sizeof(tm_result) * (size_t)nq);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -2462,7 +2484,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
     int32_t* bwin = (int32_t*)take(4 * nbw);
     int64_t* cf = (int64_t*)take(8 * ncf);
-    ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1) * (size_t)smax);
+    ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)n_parts);
 
     cudaStream_t st = b->cap;
     int rc = TM_OK;
@@ -2522,17 +2544,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
             fail(cudaGetLastError(), "k_chunkf");
         }
         if (rc == TM_OK) {
-            unsigned gm = (unsigned)(nsm * tu.blocks_per_sm);
-            int bt = tu.block_threads;
-            if (lmax <= 3 && kmax <= 4 && tu.blocks_per_sm >= 6)
-                k_match<TT, 3, 4, 6><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-            else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-            else if (lmax <= 4 && kmax <= 4 && tu.blocks_per_sm >= 4)
-                k_match<TT, 4, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-            else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-            else if (lmax <= 4) k_match<TT, 4, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-            else k_match<TT, TM_L_MAX, TM_K_MAX><<<gm, bt, match_smem_bytes(A.nq, bt), st>>>(A);
-            count_launch();
+            launch_match<TT>(A, lmax, kmax, tu, nsm, st);
             fail(cudaGetLastError(), "k_match");
         }
     }

@@ -201,6 +201,7 @@ struct QPlan {
     int64_t own_hi;
     int64_t m_total;     // |T| in q_j = r |T_j| / |T|
     int64_t sum_base;    // first per-shift sums slot of this query
+    int64_t part_base;   // first partial record of the fold (shifts x slices) of this query
     // exact three-edge queries of the same motif at smaller spans, counted in the same
     // enumeration (spans dsub[0..nsub) < delta; their counts go to the A_X* accumulators)
     int32_t nsub;

@@ -320,6 +320,53 @@ def test_bursty_10m_full_size_sampled_windows(tm, orc):
     assert res["count"] == want
 
 
+@pytest.mark.slow
+def test_bursty_10m_full_size_benchmark_batch(tm, orc):
+    """The benchmark's own 18-query batch on the full-size graph (N=1e5, M=1e7,
+    Chung-Lu 2.1 + Hawkes), in one tm_run_batch as the benchmark times it: the
+    three exact queries at delta = 86,400 that the rest of the batch rides on,
+    the smaller spans counted inside their enumeration, and the nine estimates
+    riding along, each against the oracle over the whole graph (counts
+    bit-exact as int64, estimates within 1e-12)."""
+    import os
+    import bench
+    src, dst, t = synth.bursty_100k_10m_graph()
+    g = _graph(tm, src, dst, t)
+    _, qs, meta = bench.make_queries(tm)
+    res = tm.run_batch(g, qs)
+    threads = os.cpu_count() or 8
+    for q, r, (name, delta, kind) in zip(qs, res, meta):
+        ms, md = synth.MOTIFS[name]
+        assert r["status"] == 0
+        if kind == "exact":
+            want = orc.count_exact(src, dst, t, ms, md, delta, threads=threads)
+            assert r["count"] == want, (name, delta, r["count"], want)
+        else:
+            want = orc.estimate(src, dst, t, ms, md, delta, q.c, q.p, q.seed, b=q.b, threads=threads)
+            assert _close(r["estimate"], want), (name, delta, r["estimate"], want)
+
+
+def test_fold_more_shifts_than_grid_y_and_many_slices(tm, orc):
+    """The fold loops over shifts beyond the grid's y limit (65,535) and gives every
+    query its own partial records: an estimate averaged over b = 66,000 shifts and
+    one with more than 2,048 windows per shift (folded in several slices), in one
+    batch and alone, against Algorithm 1 in the oracle."""
+    rng = np.random.default_rng(65536)
+    src, dst, t = synth.random_small_graph(rng, 5, 1000, 5000)
+    g = _graph(tm, src, dst, t)
+    ms, md = [0, 1], [1, 2]
+    mo = tm.Motif(ms, md)
+    qa = tm.estimate_query(mo, 50, 3, 0.05, 8, b=66_000)
+    qb = tm.estimate_query(mo, 2, 1, 0.5, 9, b=3)
+    want_a = orc.estimate(src, dst, t, ms, md, 50, 3, 0.05, 8, b=66_000)
+    want_b = orc.estimate(src, dst, t, ms, md, 2, 1, 0.5, 9, b=3)
+    assert want_a > 0 and want_b > 0
+    for batch in ([qa, qb], [qb, qa], [qa], [qb]):
+        for q, r in zip(batch, tm.run_batch(g, batch)):
+            assert r["status"] == 0
+            assert _close(r["estimate"], want_a if q is qa else want_b), (r, want_a, want_b)
+
+
 def test_prepared_batch_cuda_graph_matches_run_batch(tm, orc):
     """The captured CUDA graph of a batch gives the same results as tm_run_batch,
     replay after replay (scratch re-zeroed inside the graph)."""
