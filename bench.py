@@ -54,6 +54,11 @@ EST_PARAMS = {
 SEED = 2
 
 
+def est_seed(name: str, delta: int) -> int:
+    """Seed of the estimate query of (motif, delta) in the benchmark batch."""
+    return 1000 + 10 * MOTIF_NAMES.index(name) + DELTAS.index(delta)
+
+
 def max_over_ranks(x: float, world: int) -> float:
     """The largest of the ranks' values (timing is taken as the slowest replica's)."""
     if world <= 1:
@@ -172,7 +177,7 @@ def make_queries(tm):
     for i, n in enumerate(MOTIF_NAMES):
         for j, d in enumerate(DELTAS):
             c, p, b = EST_PARAMS[(n, d)]
-            qs.append(tm.estimate_query(motifs[n], d, c, p, seed=1000 + 10 * i + j, b=b))
+            qs.append(tm.estimate_query(motifs[n], d, c, p, seed=est_seed(n, d), b=b))
             meta.append((n, d, "estimate"))
     return motifs, qs, meta
 
@@ -181,97 +186,142 @@ def make_queries(tm):
 SERVE_MOTIFS = ("cycle3", "outstar3", "pingpong", "cycle4")
 
 
-def serve_mix(tm, motifs, gids, rng, n):
+def serve_mix(tm, motifs, gids, rng, n, auto=False):
     """Served query stream: graph, motif, delta, exact or estimate
-    (c in {10, 30}, p in {0.01, 0.05, 0.1}) and seed drawn uniformly."""
+    (c in {10, 30}, p in {0.01, 0.05, 0.1}) and seed drawn uniformly.  With
+    auto, estimates ask for a 5 % target relative error instead of a p
+    (TM_Q_AUTO: p chosen from a pilot's variance estimate).  Returns
+    [(graph id, query, (motif name, delta))]."""
     qs = []
     for _ in range(n):
         gi = gids[int(rng.integers(len(gids)))]
-        mo = motifs[SERVE_MOTIFS[int(rng.integers(len(SERVE_MOTIFS)))]]
+        name = SERVE_MOTIFS[int(rng.integers(len(SERVE_MOTIFS)))]
+        mo = motifs[name]
         d = int(rng.choice([600, 3600, 86400]))
         if rng.random() < 0.5:
-            qs.append((gi, tm.exact_query(mo, d)))
+            qs.append((gi, tm.exact_query(mo, d), (name, d)))
         else:
-            qs.append((gi, tm.estimate_query(mo, d, int(rng.choice([10, 30])), float(rng.choice([0.01, 0.05, 0.1])),
-                                             int(rng.integers(1 << 40)))))
+            c = int(rng.choice([10, 30]))
+            p = float(rng.choice([0.01, 0.05, 0.1]))
+            if auto:
+                q = tm.estimate_query(mo, d, c, 0.05, int(rng.integers(1 << 40)), q_mode=tm.TM_Q_AUTO)
+            else:
+                q = tm.estimate_query(mo, d, c, p, int(rng.integers(1 << 40)))
+            qs.append((gi, q, (name, d)))
     return qs
 
 
-def serve_bench(tm, graphs, rates, seconds=3.0, seed=7):
-    """Poisson arrivals at each rate for `seconds`; latency = submit -> result on
-    the host.  Returns per-rate throughput and p50/p99 latency, and the
-    one-query-per-launch plain exact counter's rate on the exact queries."""
+def serve_run(tm, srv, motifs, gids, rng, lam, seconds, auto, exact_tab):
+    """Poisson arrivals at rate lam for `seconds`; latency = submit -> result on the
+    host.  Every served estimate's relative error against the exact count of its
+    (graph, motif, delta)."""
+    n = max(8, int(lam * seconds))
+    qs = serve_mix(tm, motifs, gids, rng, n, auto)
+    gaps = rng.exponential(1.0 / lam, n)
+    pending, lat, early, done, meta_of = {}, [], {}, {}, {}
+    lock = threading.Lock()
+    state = {"done_t": 0.0}
+
+    def collector():
+        got = 0
+        while got < n:
+            x = srv.wait_any(200)
+            if x is None:
+                continue
+            now = time.perf_counter()
+            with lock:
+                done[x[0]] = (x[1], x[2])
+                t_sub = pending.pop(x[0], None)
+                if t_sub is None:      # finished before the submitter recorded it
+                    early[x[0]] = now
+                else:
+                    lat.append(now - t_sub)
+                    state["done_t"] = max(state["done_t"], now)
+            got += 1
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    nxt = t0
+    for (gi, q, key), gap in zip(qs, gaps):
+        nxt += gap
+        while True:
+            now = time.perf_counter()
+            if now >= nxt:
+                break
+            time.sleep(min(nxt - now, 0.002))
+        ts = time.perf_counter()
+        tk = srv.submit(gi, q)
+        with lock:
+            meta_of[tk] = (gi, q, key)
+            if tk in early:       # completed before we stored its submit time
+                now = early.pop(tk)
+                lat.append(now - ts)
+                state["done_t"] = max(state["done_t"], now)
+            else:
+                pending[tk] = ts
+    th.join()
+    errs, mism = [], 0
+    for tk, (gi, q, key) in meta_of.items():
+        st, r = done[tk]
+        assert st == 0, (st, key)
+        C = exact_tab[(gi,) + key]
+        if q.mode == tm.TM_MODE_EXACT:
+            mism += int(r["count"] != C)
+        else:
+            errs.append(abs(r["estimate"] - C) / C if C else (0.0 if r["estimate"] == 0 else float("inf")))
+    errs = np.array(errs)
+    el = state["done_t"] - t0
+    return {"offered_qps": lam, "queries": n, "achieved_qps": n / el,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "estimates": int(len(errs)), "estimates_within_5pct": float(np.mean(errs <= 0.05)) if len(errs) else None,
+            "estimate_rel_err_median": float(np.median(errs)) if len(errs) else None,
+            "exact_counts_checked": n - int(len(errs)), "exact_count_mismatches": mism}
+
+
+def serve_bench(tm, graphs, rates, auto_rates=(), seconds=3.0, seed=7):
+    """Continuous batching over the resident graphs at each offered rate: the
+    config mix (estimates at p in {0.01, 0.05, 0.1}) and, at auto_rates, the
+    same mix with estimates targeting 5 % relative error (TM_Q_AUTO).  Exact
+    counts of every (graph, motif, delta) come first (one batch per graph), as
+    the yardstick of the served estimates; served exact counts must equal them.
+    Also returns the one-query-per-launch plain exact counter's rate."""
     from paper_1810_00980_gb300 import synth
     motifs = {n: tm.Motif(*synth.MOTIFS[n]) for n in SERVE_MOTIFS}
-    out = []
+    keys = [(n, d) for n in SERVE_MOTIFS for d in (600, 3600, 86400)]
+    exact_tab = {}
+    t0 = time.perf_counter()
+    for gi, g in enumerate(graphs):
+        for (n, d), r in zip(keys, tm.run_batch(g, [tm.exact_query(motifs[n], d) for (n, d) in keys])):
+            exact_tab[(gi, n, d)] = r["count"]
+    exact_s = time.perf_counter() - t0
+    out, out_auto = [], []
     rng = np.random.default_rng(seed)
     with tm.Server(n_streams=2, max_batch=64, mem_budget_bytes=64 << 30) as srv:
         gids = [srv.attach(g) for g in graphs]
-        # warm-up
-        for gi, q in serve_mix(tm, motifs, gids, rng, 16):
-            srv.wait(srv.submit(gi, q), 600_000)
+        assert gids == list(range(len(graphs)))
+        for gi, q, _ in serve_mix(tm, motifs, gids, rng, 16) + serve_mix(tm, motifs, gids, rng, 8, auto=True):
+            srv.wait(srv.submit(gi, q), 600_000)   # warm-up
         for lam in rates:
-            n = max(8, int(lam * seconds))
-            qs = serve_mix(tm, motifs, gids, rng, n)
-            gaps = rng.exponential(1.0 / lam, n)
-            pending, lat, early = {}, [], {}
-            lock = threading.Lock()
-            state = {"stop": False, "done_t": 0.0}
-
-            def collector():
-                got = 0
-                while got < n:
-                    x = srv.wait_any(200)
-                    if x is None:
-                        continue
-                    now = time.perf_counter()
-                    with lock:
-                        t_sub = pending.pop(x[0], None)
-                    if t_sub is None:      # finished before the submitter recorded it
-                        with lock:
-                            early[x[0]] = now
-                        got += 1
-                        continue
-                    lat.append(now - t_sub)
-                    state["done_t"] = max(state["done_t"], now)
-                    got += 1
-
-            th = threading.Thread(target=collector, daemon=True)
-            th.start()
-            t0 = time.perf_counter()
-            nxt = t0
-            for (gi, q), gap in zip(qs, gaps):
-                nxt += gap
-                while True:
-                    now = time.perf_counter()
-                    if now >= nxt:
-                        break
-                    time.sleep(min(nxt - now, 0.002))
-                ts = time.perf_counter()
-                tk = srv.submit(gi, q)
-                with lock:
-                    if tk in early:       # completed before we stored its submit time
-                        now = early.pop(tk)
-                        lat.append(now - ts)
-                        state["done_t"] = max(state["done_t"], now)
-                    else:
-                        pending[tk] = ts
-            th.join()
-            done_t = state["done_t"]
-            el = done_t - t0
-            out.append({"offered_qps": lam, "queries": n, "achieved_qps": n / el,
-                        "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))})
+            out.append(serve_run(tm, srv, motifs, gids, rng, lam, seconds, False, exact_tab))
+        for lam in auto_rates:
+            out_auto.append(serve_run(tm, srv, motifs, gids, rng, lam, seconds, True, exact_tab))
     # one query per launch, plain exact kernel, same kind of exact queries
-    ex = [(gi, q) for gi, q in serve_mix(tm, motifs, list(range(len(graphs))), np.random.default_rng(seed + 1), 40)
-          if q.mode == tm.TM_MODE_EXACT][:12]
+    ex = [(gi, q) for gi, q, _ in serve_mix(tm, motifs, list(range(len(graphs))), np.random.default_rng(seed + 1), 60)
+          if q.mode == tm.TM_MODE_EXACT][:24]
     t0 = time.perf_counter()
     for gi, q in ex:
         tm.count_exact_plain(graphs[gi], q.motif, q.delta)
     plain = len(ex) / (time.perf_counter() - t0)
-    return {"graphs_edges": [int(g.info().m) for g in graphs], "rates": out,
-            "plain_one_query_per_launch_exact_qps": plain,
+    ok = [r for r in out_auto if (r["estimates_within_5pct"] or 0) >= 0.9]
+    best = max(ok, key=lambda r: r["achieved_qps"]) if ok else None
+    return {"graphs_edges": [int(g.info().m) for g in graphs], "rates": out, "rates_target_5pct": out_auto,
+            "best_rate_with_90pct_of_estimates_within_5pct": best,
+            "plain_one_query_per_launch_exact_qps": plain, "plain_queries": len(ex),
+            "exact_yardstick_s": exact_s,
             "mix": "graph x {cycle3, outstar3, pingpong, cycle4} x delta {600, 3600, 86400}; "
-                   "1/2 exact, 1/2 estimate c in {10, 30}, p in {0.01, 0.05, 0.1}; Poisson arrivals"}
+                   "1/2 exact, 1/2 estimate c in {10, 30}, p in {0.01, 0.05, 0.1} (rates) or a 5 % target "
+                   "relative error (rates_target_5pct, TM_Q_AUTO); Poisson arrivals"}
 
 
 # ----------------------------------------------------------- calibration ---
@@ -298,19 +348,22 @@ def calibrate(tm, g, motifs, exact, seeds=64, target=0.05, q=0.95):
 
 
 # --------------------------------------------------------- CPU baseline ---
-def cpu_baseline(src, dst, t, meta, frac=1 / 800, budget_s=25.0):
+def cpu_baseline(src, dst, t, meta, frac=1 / 800, budget_s=25.0, threads=None):
     """The oracle on a bounded sample: for every query, the first-edge prefix
-    of length frac*M (exact), or the kept windows whose first edges lie in the
-    same prefix (estimate).  Per-call fixed cost (building the oracle's own
+    of length frac*M (exact), or, for every shift of the estimate query (its own
+    seed, as the GPU batch draws them), the kept windows that start inside the
+    same time prefix (estimate).  Per-call fixed cost (building the oracle's own
     adjacency lists) is timed separately; the projected full-query time is
-    fixed + sampled / frac.  Returns queries/s for the whole step."""
+    fixed + sampled / frac for exact queries and sampled / (fraction of the
+    kept windows sampled) for estimates.  Returns queries/s for the whole step."""
     import oracle
     from paper_1810_00980_gb300 import synth
     import oracle.rng as orng
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     M = len(t)
     cut = max(1, int(M * frac))
     tn = t - t.min()
+    t_cut = int(tn[cut - 1])
     t0 = time.perf_counter()
     oracle.count_exact(src, dst, t, [0, 1, 2], [1, 2, 0], 600, threads=threads, first=(0, 0))
     fixed = time.perf_counter() - t0
@@ -327,22 +380,24 @@ def cpu_baseline(src, dst, t, meta, frac=1 / 800, budget_s=25.0):
         else:
             c, p, b = EST_PARAMS[(name, d)]
             cd = c * d
-            s = orng.shift(1000, 0, cd)
-            wins = oracle.windows_of_shift(int(tn.max()), cd, s)
-            sampled = 0
-            for (j, a, e) in wins:
-                if a > tn[cut - 1]:
-                    break
-                if orng.uniform(1000, 0, j) < p:
+            seed = est_seed(name, d)
+            n_kept = n_sampled = 0
+            for k in range(b):
+                s = orng.shift(seed, k, cd)
+                for (j, a, e) in oracle.windows_of_shift(int(tn.max()), cd, s):
+                    if orng.uniform(seed, k, j) >= p:
+                        continue
+                    n_kept += 1
+                    if a > t_cut:
+                        continue
                     lo = int(np.searchsorted(tn, a, "left"))
                     hi = int(np.searchsorted(tn, e, "right"))
                     if hi > lo:
                         oracle.count_exact_hist(src[lo:hi], dst[lo:hi], tn[lo:hi], ms, md, d, threads=threads,
                                                 n_nodes=100_000)
-                        sampled += 1
+                    n_sampled += 1
             el = time.perf_counter() - t0
-            covered = max(min(tn[cut - 1], tn.max()) / max(tn.max(), 1), 1e-9)
-            total_proj += el / covered
+            total_proj += el * n_kept / max(n_sampled, 1)
         spent += time.perf_counter() - t0
         done += 1
         if spent > budget_s:
@@ -351,9 +406,64 @@ def cpu_baseline(src, dst, t, meta, frac=1 / 800, budget_s=25.0):
     if done < len(meta):
         total_proj *= len(meta) / done
     return {"value": len(meta) / total_proj, "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": (f"first {cut} of {M} first edges per exact query (1/{int(1 / frac)}), kept windows "
-                       f"within the same time prefix per estimate query; {done}/{len(meta)} queries in "
-                       f"{spent:.1f} s; projected = oracle adjacency build ({fixed:.2f} s) + sample / fraction")}
+            "sample": (f"first {cut} of {M} first edges per exact query (1/{int(round(1 / frac))}), the kept "
+                       f"windows of every shift starting in the same time prefix per estimate query (the "
+                       f"GPU batch's seeds); {done}/{len(meta)} queries in {spent:.1f} s; projected = oracle "
+                       f"adjacency build ({fixed:.2f} s) + sample / fraction sampled")}
+
+
+def cpu_baselines(src, dst, t, meta):
+    """The oracle on all host cores, and on one thread (a smaller sample)."""
+    cb = cpu_baseline(src, dst, t, meta)
+    one = cpu_baseline(src, dst, t, meta, frac=1 / 6400, budget_s=15.0, threads=1)
+    cb["single_thread"] = {"value": one["value"], "unit": one["unit"], "cores": 1, "sample": one["sample"]}
+    return cb
+
+
+def sampled_leg(tm, torch, g, qs, meta, exact, stream, steps=5, warmup=2):
+    """The estimator's own sampled-window path on the resident graph: the nine
+    estimates of the benchmark batch in a batch of their own (no exact query of
+    their motif beside them, so none rides along and each enumerates its own
+    kept windows), with each estimate's relative error; beside them the nine
+    exact queries in one batch, each query alone in its own batched launch, and
+    (measured separately) plain one-query-per-launch exact counting.  Times are
+    CUDA events around `steps` synchronous tm_run_batch calls."""
+    sh = stream.cuda_stream
+
+    def timed(batch):
+        b = tm.Batch(g, batch)
+        for _ in range(warmup):
+            b.run(stream=sh)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            b.run(stream=sh)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps, b.results()
+
+    est = [(q, m) for q, m in zip(qs, meta) if m[2] == "estimate"]
+    exq = [(q, m) for q, m in zip(qs, meta) if m[2] == "exact"]
+    est_ms, est_res = timed([q for q, _ in est])
+    ex_ms, _ = timed([q for q, _ in exq])
+    per = {}
+    est_alone_ms = 0.0
+    for (q, (n, d, _)), r in zip(est, est_res):
+        ms, r1 = timed([q])
+        est_alone_ms += ms
+        C = exact[(n, d)]
+        per[f"{n}@{d}"] = {"c": q.c, "p": q.p, "b": q.b, "rel_err": abs(r["estimate"] - C) / C if C else None,
+                           "windows_kept": r["windows_kept"], "windows": r["windows"], "ms_alone": ms,
+                           "first_edges": r["first_edges"], "same_as_in_batch": r1[0]["estimate"] == r["estimate"]}
+    ex_alone_ms = sum(timed([q])[0] for q, _ in exq)
+    return {"estimates_batched_qps": len(est) / (est_ms / 1e3),
+            "estimates_one_per_launch_qps": len(est) / (est_alone_ms / 1e3),
+            "exact_batched_qps": len(exq) / (ex_ms / 1e3),
+            "exact_one_per_launch_qps": len(exq) / (ex_alone_ms / 1e3),
+            "estimates_rel_err_max": max(v["rel_err"] for v in per.values()),
+            "per_estimate": per,
+            "note": "estimates alone (no riders); graph resident, not rebuilt; one tm_run_batch per step"}
 
 
 # ------------------------------------------------------------------ main ---
@@ -378,31 +488,45 @@ def run_reference(args, rank):
     print(json.dumps(out))
 
 
-def run_bursty_100m_4cycle(args, tm, torch, world, rank):
+def bursty_100m_4cycle(tm, torch, steps, warmup, world=1, on_device=False):
     """Batched estimator workload: Chung-Lu (exponent 2.0) + Hawkes, N = 1e6,
     M = 1e8; the 4-cycle a->b->c->d->a at delta = 3,600 s; c in {10, 30, 100} x
     p in {0.01, 0.1} x 32 seeds = 192 estimate queries in one batched launch per
     step (after the graph ingest and adjacency build).  Errors against the
-    exact count, per (c, p): mean over seeds and the error of the 32-seed mean."""
+    exact count, per (c, p): mean over seeds and the error of the 32-seed mean.
+    on_device draws the graph with the device generator (same recipe, another
+    random stream) instead of numpy.  Returns (summary dict, timed total ms)."""
     from paper_1810_00980_gb300 import synth
-    src, dst, t = synth.bursty_1m_100m_graph()
-    M = len(t)
-    d_src, d_dst, d_t = (torch.from_numpy(x).cuda() for x in (src, dst, t))
+    if on_device:
+        d_src, d_dst, d_t = synth.chung_lu_hawkes_gpu(1_000_000, 100_000_000, 2.0, seed=3)
+    else:
+        src, dst, t = synth.bursty_1m_100m_graph()
+        d_src, d_dst, d_t = (torch.from_numpy(x).cuda() for x in (src, dst, t))
+    M = int(d_t.numel())
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     m4 = tm.Motif(*synth.MOTIFS["cycle4"])
     tm.profile_enable(True)
     g0 = tm.Graph(d_src, d_dst, d_t, stream=sh)
-    C = tm.run_batch(g0, [tm.exact_query(m4, 3600)], stream=sh)[0]["count"]
-    exact_ms = tm.profile_last()["batch_ms"]
+    ex = tm.Batch(g0, [tm.exact_query(m4, 3600)])
+    ex.run(stream=sh)
+    C = ex.results()[0]["count"]
+    exact_ms = []
+    for _ in range(3):
+        ex.run(stream=sh)
+        exact_ms.append(tm.profile_last()["batch_ms"])
     combos = [(c, p) for c in (10, 30, 100) for p in (0.01, 0.1)]
     qs = [tm.estimate_query(m4, 3600, c, p, seed=9000 + s) for (c, p) in combos for s in range(32)]
     res0 = tm.run_batch(g0, qs, stream=sh)
     errs = {}
     for i, (c, p) in enumerate(combos):
         zs = np.array([r["estimate"] for r in res0[32 * i: 32 * (i + 1)]])
-        errs[f"c={c},p={p}"] = {"mean_abs_rel_err": float(np.mean(np.abs(zs - C)) / C) if C else None,
-                                "rel_err_of_seed_mean": float(abs(zs.mean() - C) / C) if C else None}
+        e = np.abs(zs - C) / C if C else np.zeros_like(zs)
+        errs[f"c={c},p={p}"] = {"mean_abs_rel_err": float(e.mean()), "max_abs_rel_err": float(e.max()),
+                                "within_5pct": float(np.mean(e <= 0.05)),
+                                "rel_err_of_seed_mean": float(abs(zs.mean() - C) / C) if C else None,
+                                "windows_kept_mean": float(np.mean([r["windows_kept"] for r in res0[32 * i: 32 * (i + 1)]])),
+                                "windows": int(res0[32 * i]["windows"])}
     g0.free()
 
     def step():
@@ -413,7 +537,7 @@ def run_bursty_100m_4cycle(args, tm, torch, world, rank):
             g.free()
         return b
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b = step()
     torch.cuda.synchronize()
     if world > 1:
@@ -422,41 +546,63 @@ def run_bursty_100m_4cycle(args, tm, torch, world, rank):
     launches0 = tm.profile_last()["launches"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    match_ms = []
+    match_ms, prof = [], []
     with ClockSampler(torch.cuda.current_device()) as clk:
         clk_t0 = time.time()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b = step()
-            match_ms.append(tm.profile_last()["match_ms"])
+            p_ = tm.profile_last()
+            prof.append(p_)
+            match_ms.append(p_["match_ms"])
         e1.record(stream)
         torch.cuda.synchronize()
         clk_t1 = time.time()
-        torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
-    total_ms = max_over_ranks(total_ms, world)
     results = b.results()
     launches = tm.profile_last()["launches"] - launches0
     b_match = sum(12 * r["cand_edges"] + 16 * r["last_ranges"] + 8 * r["inst_read"] for r in results)
     mm = statistics.median(match_ms)
     hbm = peaks().get("hbm_gbs") or 6800.0
     achieved = b_match / (mm / 1e3) / 1e9 if mm > 0 else 0.0
-    if rank != 0:
-        return
+    del d_src, d_dst, d_t
+    torch.cuda.empty_cache()
     out = {
-        "metric": METRIC, "value": whole_job_rate(len(qs), args.steps, world, total_ms), "unit": "queries/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "Chung-Lu exponent 2.0 + Hawkes, N=1,000,000, M=100,000,000, 2 years; "
-                               "4-cycle, delta=3600; c {10,30,100} x p {0.01,0.1} x 32 seeds = 192 estimate "
-                               "queries in one batched launch; graph ingest + adjacency build per step",
-                   "queries_per_step": len(qs), "edges": M, "l2": "inputs larger than L2"},
-        "exact_count": C, "exact_batch_ms": exact_ms, "errors": errs,
+        "workload": "Chung-Lu exponent 2.0 + Hawkes, N=1,000,000, M=100,000,000, 2 years" +
+                    (" (drawn on the device)" if on_device else "") + "; 4-cycle, delta=3600; c {10,30,100} x p "
+                    "{0.01,0.1} x 32 seeds = 192 estimate queries in one batched launch; graph ingest + adjacency "
+                    "build per step",
+        "queries_per_step": len(qs), "edges": M, "steps": steps, "warmup": warmup,
+        "ms_per_step": total_ms / steps, "queries_per_s": world * len(qs) * steps / (total_ms / 1e3),
+        "exact_count": C, "exact_batch_ms": statistics.median(exact_ms),
+        "exact_queries_per_s_one_per_launch": 1e3 / statistics.median(exact_ms),
+        "errors": errs,
         "first_edges_per_step": sum(r["first_edges"] for r in results),
+        "phases_ms": {k: statistics.median(p_[k] for p_ in prof)
+                      for k in ("graph_ms", "windows_ms", "level2_ms", "match_ms", "fold_ms")},
         "roofline": {"kernel": "k_match", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "algorithmic_bytes": b_match, "launch_ms": mm},
         "gpu_launches": launches, "clocks": clk.summary(clk_t0, clk_t1),
     }
+    return out, total_ms
+
+
+def run_bursty_100m_4cycle(args, tm, torch, world, rank):
+    """The batched-estimator workload on its own (numpy-drawn graph, as the tests draw it)."""
+    leg, total_ms = bursty_100m_4cycle(tm, torch, args.steps, args.warmup, world)
+    total_ms = max_over_ranks(total_ms, world)
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": whole_job_rate(leg["queries_per_step"], args.steps, world, total_ms),
+        "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": leg["workload"], "queries_per_step": leg["queries_per_step"], "edges": leg["edges"],
+                   "l2": "inputs larger than L2"},
+    }
+    out.update({k: v for k, v in leg.items() if k not in ("workload", "queries_per_step", "edges", "steps",
+                                                          "warmup", "ms_per_step", "queries_per_s")})
     print(json.dumps(out))
 
 
@@ -550,9 +696,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--serve-full", action="store_true",
-                    help="serving run on four resident graphs of 1M, 10M, 25M and 50M edges")
+    ap.add_argument("--serve-small", action="store_true",
+                    help="serving run on two resident graphs (1M and 10M edges) instead of four (1M, 10M, 25M, 50M)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-sampled", action="store_true", help="skip the estimates-alone measurement")
+    ap.add_argument("--no-4cycle", action="store_true",
+                    help="skip the 1e8-edge batched-estimator measurement (192 4-cycle estimates)")
     ap.add_argument("--no-stream", action="store_true", help="skip the host-streaming measurement")
     ap.add_argument("--workload", default="bursty-10m", choices=["bursty-10m", "bursty-100m-4cycle", "hubs-1b"])
     ap.add_argument("--tuning", default="auto",
@@ -699,6 +848,13 @@ def main():
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_s = max_over_ranks(e2e_s, world)
 
+    # the estimator's sampled-window path on its own (no riding along), beside exact counting
+    sampled = None
+    if not args.no_sampled:
+        g_s = tm.Graph(d_src, d_dst, d_t, stream=sh)
+        sampled = sampled_leg(tm, torch, g_s, qs, meta, exact, stream)
+        g_s.free()
+
     # streaming: the same batch over the edge list in pinned host memory, in chronological
     # segments (outside the timed step); results must equal the resident batch's
     stream_res = None
@@ -737,22 +893,26 @@ def main():
     serve = None
     if not args.no_serve:
         from paper_1810_00980_gb300 import synth
-        if args.serve_full:
-            sizes = (1_000_000, 10_000_000, 25_000_000, 50_000_000)
-        else:
-            sizes = (1_000_000, 10_000_000)
+        sizes = (1_000_000, 10_000_000) if args.serve_small else (1_000_000, 10_000_000, 25_000_000, 50_000_000)
         sgraphs = []
         for i, m_e in enumerate(sizes):
             if m_e == M:
-                s_, d_, t_ = src, dst, t
-            else:
-                s_, d_, t_ = synth.chung_lu_hawkes(max(10_000, m_e // 100), m_e, 2.1, seed=40 + i)
-            sgraphs.append(tm.Graph(torch.from_numpy(s_).cuda(), torch.from_numpy(d_).cuda(),
-                                    torch.from_numpy(t_).cuda()))
+                ds_, dd_, dt_ = d_src, d_dst, d_t
+            else:   # the same recipe drawn on the device (numpy would take minutes at 5e7 edges)
+                ds_, dd_, dt_ = synth.chung_lu_hawkes_gpu(max(10_000, m_e // 100), m_e, 2.1, seed=40 + i)
+            sgraphs.append(tm.Graph(ds_, dd_, dt_))
+            del ds_, dd_, dt_
         torch.cuda.synchronize()
-        serve = serve_bench(tm, sgraphs, rates=(20, 100, 400, 1600))
+        # offered rates around the server's capacity on these graphs (a few tens of queries/s:
+        # the largest graph's 4-cycle and three-edge queries at delta = 86,400 take tens of ms)
+        serve = serve_bench(tm, sgraphs, rates=(10, 25, 50, 100), auto_rates=(10, 25, 50))
         for gg in sgraphs:
             gg.free()
+
+    # the batched estimator at 1e8 edges: 192 estimate queries of the 4-cycle per launch
+    c3 = None
+    if not args.no_4cycle:
+        c3, _ = bursty_100m_4cycle(tm, torch, steps=3, warmup=1, world=world, on_device=True)
 
     # roofline of the dominant kernel (the longer of k_level2 and k_match)
     pk = peaks()
@@ -795,7 +955,7 @@ def main():
         return
     cb = None
     if not args.no_cpu_baseline:
-        cb = cpu_baseline(src, dst, t, meta)
+        cb = cpu_baselines(src, dst, t, meta)
     p_last = prof[-1] if prof else {}
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -818,7 +978,9 @@ def main():
         "cpu_baseline": cb,
         "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 16 * M,
                 "d2h_bytes_per_step": nq * ctypes.sizeof(tm.ResultC)},
+        "sampled": sampled,
         "serve": serve,
+        "bursty_100m_4cycle": c3,
         "stream": stream_res,
         "q_corr_edges_vs_weight": q_corr,
         "gpu_launches": launches,

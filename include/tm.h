@@ -206,7 +206,7 @@ int tm_run_batch(const tm_graph* g, const tm_query* queries, int32_t n_queries,
  * because cudaMalloc/cudaFree can block and synchronise the device.  It calls
  * no cudaMalloc, cudaFree or other allocating routine.  Its scratch is one
  * static device array compiled into the library, TM_NOALLOC_SCRATCH_BYTES
- * (about 7.4 MB) on every GPU that loads the library, held until the process
+ * (about 14.7 MB) on every GPU that loads the library, held until the process
  * exits.
  *   g       graph with at most TM_NOALLOC_MAX_EDGES edges (else TM_EINVAL), loaded on
  *           the current device (else TM_EINVAL: the array used is the current device's).
@@ -221,7 +221,7 @@ int tm_run_batch(const tm_graph* g, const tm_query* queries, int32_t n_queries,
  * serialise them.  Errors: TM_EINVAL, TM_ENOMEM, TM_ECUDA, TM_EOVERFLOW;
  * tm_last_error is not updated. */
 #define TM_NOALLOC_MAX_EDGES 262144
-#define TM_NOALLOC_SCRATCH_BYTES 7347200
+#define TM_NOALLOC_SCRATCH_BYTES 14687232
 int tm_count_exact_noalloc(const tm_graph* g, const tm_motif* m, int64_t delta, void* stream,
                            int64_t* count);
 
@@ -289,7 +289,10 @@ typedef struct {
 int tm_get_tuning(tm_tuning* out);
 int tm_set_tuning(const tm_tuning* in);
 /* Time candidate tunings on `queries` over g (results discarded) and keep the
- * fastest; *best receives it.  Synchronous. */
+ * fastest; *best receives it.  Candidates: 128 or 256 threads, 4, 6, 8 or 12
+ * blocks per SM, chunks of 256, 1024 or 4096 items, and (only when the batch
+ * has an exact query whose last edge is counted on a node view) thresholds 32
+ * and 128; each is timed as the median of three whole batches.  Synchronous. */
 int tm_autotune(const tm_graph* g, const tm_query* queries, int32_t n_queries, tm_tuning* best);
 
 /* ---- profiling ----------------------------------------------------------------

@@ -244,9 +244,17 @@ int tm_set_tuning(const tm_tuning* in) {
 int tm_autotune(const tm_graph* g, const tm_query* queries, int32_t n_queries, tm_tuning* best) {
     if (!g || !queries || n_queries <= 0 || !best) { set_error("bad argument"); return TM_EINVAL; }
     const int bts[] = {128, 256};
-    const int bpss[] = {2, 4, 6, 8};
-    const int chunks[] = {64, 256, 1024};
-    const int thr[] = {32, 128};
+    const int bpss[] = {4, 6, 8, 12};
+    const int chunks[] = {256, 1024, 4096};
+    // the range threshold only matters for exact queries whose last edge has one bound
+    // endpoint (two-edge motifs, or deeper ones closing on a node view)
+    bool thr_matters = false;
+    for (int i = 0; i < n_queries; i++) {
+        const tm_motif* m = queries[i].motif;
+        if (m && queries[i].mode == TM_MODE_EXACT && m->l >= 2 && m->lv[m->l - 1].view != kPair) thr_matters = true;
+    }
+    const int thr_all[] = {32, 128};
+    const int n_thr = thr_matters ? 2 : 1;
     std::vector<tm_result> res((size_t)n_queries);
     cudaStream_t st = thread_stream();
     cudaEvent_t e0, e1;
@@ -261,29 +269,29 @@ int tm_autotune(const tm_graph* g, const tm_query* queries, int32_t n_queries, t
     for (int bt : bts)
         for (int bps : bpss)
             for (int ch : chunks)
-                for (int th : thr) {
+                for (int ti = 0; ti < n_thr; ti++) {
                     if (rc != TM_OK) break;
                     Tuning t;
                     t.block_threads = bt;
                     t.blocks_per_sm = bps;
                     t.chunk_items = ch;
-                    t.enum_threshold = th;
+                    t.enum_threshold = thr_matters ? thr_all[ti] : saved.enum_threshold;
                     {
                         std::lock_guard<std::mutex> lk(g_tune_mu);
                         tuning() = t;
                     }
-                    float ms = 1e30f;
-                    for (int rep = 0; rep < 2 && rc == TM_OK; rep++) {
+                    // the median of three whole batches (one slow outlier does not pick a tuning)
+                    float ms3[3] = {1e30f, 1e30f, 1e30f};
+                    for (int rep = 0; rep < 3 && rc == TM_OK; rep++) {
                         cudaEventRecord(e0, st);
                         rc = run_batch(g, queries, n_queries, res.data(), st, nullptr);
                         cudaEventRecord(e1, st);
                         cudaEventSynchronize(e1);
-                        float x = 0.f;
-                        cudaEventElapsedTime(&x, e0, e1);
-                        ms = std::min(ms, x);
+                        cudaEventElapsedTime(&ms3[rep], e0, e1);
                     }
-                    if (rc == TM_OK && ms < best_ms) {
-                        best_ms = ms;
+                    std::sort(ms3, ms3 + 3);
+                    if (rc == TM_OK && ms3[1] < best_ms) {
+                        best_ms = ms3[1];
                         bestt = t;
                     }
                 }

@@ -266,6 +266,8 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     int dev = 0;
     TM_CUDA(cudaGetDevice(&dev));
     PhaseEvents pe(profiling());
+    NvtxPhases nv;
+    nv.next("tm_graph_build");
     int ev0 = pe.mark(st);
     int64_t tmin = 0, tmax = 0;
     int32_t loops = 0;

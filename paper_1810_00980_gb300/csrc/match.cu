@@ -20,6 +20,7 @@
 //              query: Z_k = sum_j W_j / q_j per shift and the mean over shifts
 //              (Algorithm 1's return value).
 #include <algorithm>
+#include <limits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -62,6 +63,21 @@ struct WinDev {
     unsigned long long* acc;  // [NW][A_N]
 };
 
+// What the matcher needs of a first edge that has items, in one record that k_level2 writes
+// (32 bytes with 32-bit times): each item starts from one load instead of a chain through
+// the window table, the plan and the edge arrays.
+template <typename TT>
+struct FRec {
+    int32_t s1, d1;   // the first edge's nodes
+    int32_t win;      // its window slot
+    int32_t q;        // its query
+    TT t1;            // its time
+    TT thi;           // last time an instance starting there may use (clamped to TT's range,
+                      // which holds every edge time)
+    int64_t lo2;      // start of its items in their view (negative: closing-side items)
+};
+static_assert(sizeof(FRec<int32_t>) == 32 && sizeof(FRec<int64_t>) == 40, "first-edge record layout");
+
 template <typename TT>
 struct MatchArgs {
     GraphDevT<TT> G;
@@ -71,8 +87,7 @@ struct MatchArgs {
     int64_t NW;
     int64_t F;
     const int64_t* d_F;    // if set, the first-edge count is read here on the device
-    const int32_t* fwin;   // [F] window of each first edge
-    const int64_t* lo2;    // [F] start of its second-edge candidate range
+    const FRec<TT>* rec;   // [F] record of each first edge with items
     const int64_t* excl;   // [F] exclusive scan of the range lengths
     const int64_t* hs_a;   // [F] closing pair range start (queries whose last edge is fixed by the first)
     const int64_t* hs_hi;  // [F] closing pair range end
@@ -83,6 +98,7 @@ struct MatchArgs {
     const int32_t* blockwin = nullptr;  // [ceil(F/32)] window of first edge 32 b (null: searched)
     const int64_t* chunkf = nullptr;    // [nchunkf] first edge of work item i * chunk (null: searched)
     int64_t nchunkf = 0;
+    bool ride = false;                  // estimates ride along with exact queries of the batch
 };
 
 // ----------------------------------------------------------------- helpers
@@ -396,9 +412,50 @@ __device__ __forceinline__ void ride_window(const QPlan& R, int k, int64_t t1, i
     thi = min(t1 + R.delta, s + (j + 1) * R.cd - 1);
 }
 
+// Rider sums go through a per-block table in shared memory keyed by window (when c delta is
+// long, a handful of windows take most instances, and the same few global words would
+// otherwise be hit by every SM), flushed to the global sums when the block ends.  The table
+// sits at the end of k_match's dynamic shared memory (batches with riders only).
+constexpr int kRideTab = 128;
+constexpr unsigned long long kTabFree = ~0ull;
+constexpr unsigned long long kInstKey = 1ull << 62;   // key flag: an exact query's entries-read counter
+struct RideTab {
+    unsigned long long key[kRideTab];   // window index (with kInstKey: the A_INST counter of that
+                                        // window), kTabFree when unused
+    unsigned long long cnt[kRideTab];
+    unsigned long long lo[kRideTab];    // the Q64 weight sum: lo word, then the integer part
+    unsigned long long hi[kRideTab];
+};
+__device__ __forceinline__ RideTab* ride_tab() {
+    extern __shared__ __align__(16) unsigned char smem_plans[];
+    uint32_t n;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(n));
+    return reinterpret_cast<RideTab*>(smem_plans + n - sizeof(RideTab));
+}
+
+// cnt instances with Q64 weight sum (lo, hi) into rider window w: the block's table when the
+// window has (or takes) its slot there, else the global sums
 __device__ __forceinline__ void ride_add(unsigned long long* acc, int64_t w, unsigned long long cnt,
                                          unsigned long long lo, unsigned long long hi) {
     if (!cnt) return;
+    RideTab* tab = ride_tab();
+    const int sl = (int)(w & (kRideTab - 1));
+    unsigned long long key = *(volatile unsigned long long*)&tab->key[sl];
+    if (key == kTabFree) {
+        unsigned long long old = atomicCAS(&tab->key[sl], kTabFree, (unsigned long long)w);
+        key = old == kTabFree ? (unsigned long long)w : old;
+    }
+    if (key == (unsigned long long)w) {
+        atomicAdd(&tab->cnt[sl], cnt);
+        unsigned long long old = atomicAdd(&tab->lo[sl], lo);
+        if (old + lo < old) hi += 1;
+        if (hi) atomicAdd(&tab->hi[sl], hi);
+        return;
+    }
+    if ((unsigned long long)w & kInstKey) {
+        atomicAdd(acc + ((unsigned long long)w & ~kInstKey) * A_N + A_INST, cnt);
+        return;
+    }
     unsigned long long* p = acc + w * A_N;
     atomicAdd(p + A_COUNT, cnt);
     atomic_add_u128(p + A_WLO, lo, hi);
@@ -424,10 +481,11 @@ __device__ __noinline__ void ride_at(const QPlan* __restrict__ PL, const QPlan& 
     for (int r = 0; r < Q.nride; r++) {
         const QPlan& R = PL[Q.ride_q[r]];
         if (t3 - t1 > R.delta) continue;
+        const bool all_kept = R.q_mode == TM_Q_UNIFORM && R.p >= 1.0;   // no keep flag to read
         for (int k = 0; k < R.b; k++) {
             int64_t w, thi;
             ride_window(R, k, t1, w, thi);
-            if (t3 > thi || !kept[w]) continue;
+            if (t3 > thi || !(all_kept || kept[w])) continue;
             unsigned long long lo, hi;
             ride_weight(R, t3 - t1, cnt, lo, hi);
             ride_add(acc, w, cnt, lo, hi);
@@ -435,19 +493,22 @@ __device__ __noinline__ void ride_at(const QPlan* __restrict__ PL, const QPlan& 
     }
 }
 
-// one instance per closing entry of the time-sorted range [lo, hi) (entries after tc)
+// one instance per closing entry of the time-sorted range [lo, hi) (entries after tc); the most
+// entries read for one rider shift count as the exact query's last-edge entries read one by one
 template <typename TT>
 __device__ __noinline__ void ride_range(const QPlan* __restrict__ PL, const QPlan& Q,
                                         const int32_t* __restrict__ kept, unsigned long long* acc,
                                         const TT* __restrict__ ta, int64_t clo, int64_t chi, int64_t t1,
                                         int64_t tc) {
+    unsigned long long nread = 0;
     for (int r = 0; r < Q.nride; r++) {
         const QPlan& R = PL[Q.ride_q[r]];
         if (t1 + R.delta <= tc) continue;   // no closing edge after tc fits the span
+        const bool all_kept = R.q_mode == TM_Q_UNIFORM && R.p >= 1.0;   // no keep flag to read
         for (int k = 0; k < R.b; k++) {
             int64_t w, thi;
             ride_window(R, k, t1, w, thi);
-            if (thi <= tc || !kept[w]) continue;
+            if (thi <= tc || !(all_kept || kept[w])) continue;
             unsigned long long cnt = 0, wl = 0, wh = 0;
             for (int64_t x = clo; x < chi; x++) {
                 int64_t t3 = (int64_t)ta[x];
@@ -460,8 +521,10 @@ __device__ __noinline__ void ride_range(const QPlan* __restrict__ PL, const QPla
                 cnt++;
             }
             ride_add(acc, w, cnt, wl, wh);
+            nread = max(nread, cnt);
         }
     }
+    if (nread) ride_add(acc, (int64_t)(kInstKey | (unsigned long long)Q.win_base), nread, 0, 0);
 }
 
 // n instances of duration dur at once: n * (wi + wf 2^-64), exactly as n single adds
@@ -506,9 +569,10 @@ __device__ __forceinline__ const QPlan* stage_plans(const QPlan* gplans, int nq,
 
 static_assert(kSmemPlans == 64, "acc_smem_offset assumes 64 staged plans at most");
 
-// dynamic shared memory of k_level2 / k_match: plans, then the accumulator slots
-size_t match_smem_bytes(int nq, int threads) {
-    return acc_smem_offset(nq) + (size_t)(A_N - A_NREG) * 8 * (size_t)threads;
+// dynamic shared memory of k_level2 / k_match: plans, then the accumulator slots, then (k_match
+// of a batch with riders) the rider table
+size_t match_smem_bytes(int nq, int threads, bool ride_tab = false) {
+    return acc_smem_offset(nq) + (size_t)(A_N - A_NREG) * 8 * (size_t)threads + (ride_tab ? sizeof(RideTab) : 0);
 }
 
 // ----------------------------------------------------------------- kernels
@@ -654,9 +718,9 @@ __global__ void k_chunkf(const int64_t* __restrict__ excl, int64_t Fh, const int
 
 // one warp-uniform grid-stride loop over first edges f
 template <typename TT>
-__global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __restrict__ fwin,
-                                                int32_t* __restrict__ len2, int64_t* __restrict__ lo2,
-                                                int64_t* __restrict__ hs_a, int64_t* __restrict__ hs_hi) {
+__global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, FRec<TT>* __restrict__ rec,
+                                                int32_t* __restrict__ len2, int64_t* __restrict__ hs_a,
+                                                int64_t* __restrict__ hs_hi) {
     const GraphDevT<TT>& G = A.G;
     extern __shared__ __align__(16) unsigned char smem_plans[];
     const QPlan* PL = stage_plans(A.plans, A.nq, smem_plans);
@@ -772,15 +836,17 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                             int64_t thr = t1;
                             for (int r = 0; r < Q.nride; r++) {
                                 const QPlan& R = PL[Q.ride_q[r]];
+                                const bool all_kept = R.q_mode == TM_Q_UNIFORM && R.p >= 1.0;
                                 for (int k = 0; k < R.b; k++) {
                                     int64_t w, th;
                                     ride_window(R, k, t1, w, th);
-                                    if (A.W.kept[w]) thr = max(thr, th);
+                                    if (all_kept || A.W.kept[w]) thr = max(thr, th);
                                 }
                             }
                             if (thr > t1) {
                                 len = gallop_ub(G.pair_t, ha, hh, thr) - ha;   // items for the riders only
                                 hh = le2;
+                                acc.s(A_INST) += (unsigned long long)len;   // last edges read one by one
                             }
                         }
                     } else {
@@ -867,12 +933,21 @@ __global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, int32_t* __r
                 }
             }
         }
-        fwin[f] = (int32_t)wi;
         len2[f] = (int32_t)len;   // a range inside one view: below 2^31
-        lo2[f] = lo;
-        if (hs_a) {
-            hs_a[f] = ha;
-            hs_hi[f] = hh;
+        if (len > 0) {            // the matcher reads these only for first edges with items
+            FRec<TT> r;
+            r.s1 = s1;
+            r.d1 = d1;
+            r.win = (int32_t)wi;
+            r.q = A.W.q[wi];
+            r.t1 = (TT)t1;
+            r.thi = (TT)min(thi, (int64_t)std::numeric_limits<TT>::max());
+            r.lo2 = lo;
+            rec[f] = r;
+            if (hs_a) {
+                hs_a[f] = ha;
+                hs_hi[f] = hh;
+            }
         }
     }
     acc_flush_warp(acc, A.W.acc);
@@ -1035,6 +1110,14 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
     Acc acc;
     acc_init(acc, smem_plans, A.nq);
     acc_zero(acc);
+    if (A.ride) {
+        RideTab* tab = ride_tab();
+        for (int i = threadIdx.x; i < kRideTab; i += blockDim.x) {
+            tab->key[i] = kTabFree;
+            tab->cnt[i] = tab->lo[i] = tab->hi[i] = 0;
+        }
+        __syncthreads();
+    }
     for (;;) {
         unsigned long long c0u = 0;
         if (lane == 0) c0u = atomicAdd(A.counter, (unsigned long long)A.chunk);
@@ -1081,14 +1164,15 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
             bool deeper = false;
             if (valid) {
                 int64_t f = fw;
-                win = A.fwin[f];
-                q = A.W.q[win];
+                const FRec<TT> r = A.rec[f];
+                win = r.win;
+                q = r.q;
                 const QPlan& Q = PL[q];
-                int64_t e1 = A.W.lo[win] + (f - A.W.fbase[win]);
-                if (Q.full) e1 = __ldg(Q.perm + e1);
-                first_edge(G, Q.order, e1, phi[0], phi[1], t1);
-                thi = first_thi(Q, A.W, win, t1);
-                int64_t l2 = A.lo2[f];
+                phi[0] = r.s1;
+                phi[1] = r.d1;
+                t1 = (int64_t)r.t1;
+                thi = (int64_t)r.thi;
+                int64_t l2 = r.lo2;
                 if (Q.ex23) {
                     // two-node motif: item = last edge j; its middle edges number
                     // (middle-pair edges before t_j) - (those at or before t1)
@@ -1225,6 +1309,21 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
         acc_flush_warp(acc, A.W.acc);
     }
     acc_flush_warp(acc, A.W.acc);
+    if (A.ride) {   // every warp of the block is done: the rider sums go to the global windows
+        RideTab* tab = ride_tab();
+        __syncthreads();
+        for (int i = threadIdx.x; i < kRideTab; i += blockDim.x) {
+            const unsigned long long key = tab->key[i];
+            if (key == kTabFree) continue;
+            if (key & kInstKey) {
+                atomicAdd(A.W.acc + (key & ~kInstKey) * A_N + A_INST, tab->cnt[i]);
+                continue;
+            }
+            unsigned long long* p = A.W.acc + (int64_t)key * A_N;
+            if (tab->cnt[i]) atomicAdd(p + A_COUNT, tab->cnt[i]);
+            atomic_add_u128(p + A_WLO, tab->lo[i], tab->hi[i]);
+        }
+    }
 }
 
 // Windows of one shift that a block of k_fold_shift sums: a query's shifts are cut into
@@ -1392,7 +1491,7 @@ template <typename TT>
 void launch_match(const MatchArgs<TT>& A, int lmax, int kmax, const Tuning& tu, int nsm, cudaStream_t st) {
     const int bps = tu.blocks_per_sm, bt = tu.block_threads;
     const unsigned gm = (unsigned)(nsm * bps);
-    const size_t sm = match_smem_bytes(A.nq, bt);
+    const size_t sm = match_smem_bytes(A.nq, bt, A.ride);
     if (lmax <= 3 && kmax <= 4 && bps >= 6) k_match<TT, 3, 4, 6><<<gm, bt, sm, st>>>(A);
     else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, sm, st>>>(A);
     else if (lmax <= 4 && kmax <= 4 && bps >= 4) k_match<TT, 4, 4, 4><<<gm, bt, sm, st>>>(A);
@@ -1614,10 +1713,10 @@ int ex_tables_for(const tm_graph* g, const std::vector<QPlan>& hp, cudaStream_t 
 // per-first-edge scratch of one batch: window, second-level range start and length, the
 // exclusive scan of the lengths, the hoisted closing ranges, and the block-window and
 // chunk-start tables
-size_t per_first_scratch_bytes(int64_t F, bool hoist) {
+size_t per_first_scratch_bytes(int64_t F, bool hoist, size_t rec_bytes) {
     size_t Fs = (size_t)std::max<int64_t>(F, 1);
     size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
-    return 2 * a256(4 * Fs) + (hoist ? 4 : 2) * a256(8 * Fs) + a256(4 * nbw) + a256(8 * ncf);
+    return a256(rec_bytes * Fs) + a256(4 * Fs) + (hoist ? 3 : 1) * a256(8 * Fs) + a256(4 * nbw) + a256(8 * ncf);
 }
 constexpr size_t kBoundScratchBytes = (size_t)2 << 30;
 
@@ -1769,6 +1868,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         if (rc == TM_OK && e != cudaSuccess) rc = cuda_status(e, what, __FILE__, __LINE__);
     };
     PhaseEvents pe(profiling());
+    NvtxPhases nv;
+    nv.next("tm_windows");
     auto wall0 = std::chrono::steady_clock::now();
     int ev_w0 = pe.mark(st), ev_w1 = -1, ev_l0 = -1, ev_l1 = -1, ev_l2 = -1, ev_m1 = -1, ev_f1 = -1;
     int64_t hW2 = 0;
@@ -1820,9 +1921,10 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     // The per-first-edge scratch is sized for the bound on F when that fits in
     // kBoundScratchBytes, and the kernels read F on the device: no host round trip
     // between the window partition and the matcher.  Otherwise F is read back first.
-    const bool bounded = F_ub > 0 && per_first_scratch_bytes(F_ub, any_hoist) <= kBoundScratchBytes;
+    const bool bounded = F_ub > 0 && per_first_scratch_bytes(F_ub, any_hoist, sizeof(FRec<TT>)) <= kBoundScratchBytes;
     int64_t F = 0;
     ev_w1 = pe.mark(st);
+    nv.next("tm_sizing");
     if (rc == TM_OK && !bounded) {
         fail(cudaMemcpyAsync(&F, dF, 8, cudaMemcpyDeviceToHost, st), "F readback");
         fail(cudaStreamSynchronize(st), "sync F");
@@ -1832,12 +1934,11 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     if (rc == TM_OK && Fa > 0) {
         size_t Fs = (size_t)Fa;
         size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
-        rc = scratch_acquire(per_first_scratch_bytes(Fa, any_hoist), st, fb);
+        rc = scratch_acquire(per_first_scratch_bytes(Fa, any_hoist, sizeof(FRec<TT>)), st, fb);
         if (rc == TM_OK) {
             char* q2 = (char*)fb.p;
             auto take2 = [&](size_t bytes) { char* r = q2; q2 += a256(bytes); return (void*)r; };
-            int32_t* fwin = (int32_t*)take2(4 * Fs);
-            int64_t* lo2 = (int64_t*)take2(8 * Fs);
+            FRec<TT>* rec = (FRec<TT>*)take2(sizeof(FRec<TT>) * Fs);
             int64_t* excl = (int64_t*)take2(8 * Fs);   // exclusive scan of the range lengths
             int32_t* len32 = (int32_t*)take2(4 * Fs);
             int64_t* hs_a = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
@@ -1847,19 +1948,22 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             MatchArgs<TT> A;
             const int64_t* d_Fk = bounded ? dF : nullptr;
             A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = Fa; A.d_F = d_Fk;
-            A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
+            A.rec = rec; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
             A.d_W2 = dW2; A.counter = dctr;
             A.enum_threshold = tu.enum_threshold;
             A.chunk = tu.chunk_items;
             A.blockwin = bwin; A.chunkf = cf; A.nchunkf = (int64_t)ncf;
+            A.ride = !h_shifts.empty();
             int64_t gl2 = std::min<int64_t>((Fa + 255) / 256, (int64_t)nsm * 8);
             k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
                 W.fbase, NW, Fa, d_Fk, bwin);
             count_launch();
             ev_l0 = pe.mark(st);
-            k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, len32, lo2, hs_a, hs_hi); count_launch();
+            nv.next("tm_level2");
+            k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, rec, len32, hs_a, hs_hi); count_launch();
             fail(cudaGetLastError(), "k_level2");
             ev_l2 = pe.mark(st);
+            nv.next("tm_scan");
             if (rc == TM_OK) rc = scan_lengths(len32, excl, Fa, d_Fk, dW2, nullptr, 0, st);
             if (rc == TM_OK) {
                 k_chunkf<<<(unsigned)std::min<int64_t>(((int64_t)ncf + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
@@ -1868,6 +1972,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                 fail(cudaGetLastError(), "k_chunkf");
             }
             ev_l1 = pe.mark(st);
+            nv.next("tm_match");
             if (rc == TM_OK) {
                 launch_match<TT>(A, lmax, kmax, tu, nsm, st);
                 fail(cudaGetLastError(), "k_match");
@@ -1879,10 +1984,12 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     }
     if (rc == TM_OK) {
         int ev_f0 = pe.mark(st);
+        nv.next("tm_fold");
         launch_fold(dplans, nq, bmax, smax, W, dpart, dres, dbg && dbg->sums ? dsums : nullptr,
                     dbg && dbg->sub_count ? dsubc : nullptr, st);
         fail(cudaGetLastError(), "fold");
         ev_f1 = pe.mark(st);
+        nv.next(nullptr);
         if (ev_m1 < 0) ev_m1 = ev_f0;
     }
     if (rc == TM_OK) fail(cudaMemcpyAsync(res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
@@ -2196,8 +2303,9 @@ constexpr size_t na_a256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int64_t kNaMaxEdges = TM_NOALLOC_MAX_EDGES;
 constexpr int64_t kNaWsElems = 2 * ((kNaMaxEdges + 2047) / 2048);
 constexpr size_t kNaWinBytes = 13 * 256 + na_a256(8 * tmo::A_N);
+constexpr size_t kNaRecBytes = 40;   // the first-edge record with 64-bit times (the larger one)
 constexpr size_t kNaBytes = na_a256(sizeof(tmo::QPlan)) + na_a256(sizeof(tm_result)) + kNaWinBytes +
-                            3 * 256 + na_a256(4 * kNaMaxEdges) + 3 * na_a256(8 * kNaMaxEdges) +
+                            3 * 256 + na_a256(kNaRecBytes * kNaMaxEdges) + 2 * na_a256(8 * kNaMaxEdges) +
                             na_a256(8 * kNaWsElems);
 static_assert(kNaBytes == TM_NOALLOC_SCRATCH_BYTES, "tm.h states the scratch size");
 constexpr int kNaMaxDevices = 64;
@@ -2271,9 +2379,9 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
     int64_t* dF = (int64_t*)take(8);
     int64_t* dW2 = (int64_t*)take(8);
     unsigned long long* dctr = (unsigned long long*)take(8);
-    int32_t* fwin = (int32_t*)take(4 * (size_t)kNaMaxEdges);
+    static_assert(sizeof(FRec<TT>) <= kNaRecBytes, "record size of the static scratch");
+    FRec<TT>* rec = (FRec<TT>*)take(kNaRecBytes * (size_t)kNaMaxEdges);
     int64_t* len2 = (int64_t*)take(8 * (size_t)kNaMaxEdges);
-    int64_t* lo2 = (int64_t*)take(8 * (size_t)kNaMaxEdges);
     int64_t* excl = (int64_t*)take(8 * (size_t)kNaMaxEdges);
     int64_t* ws = (int64_t*)take(8 * (size_t)kNaWsElems);
     if ((size_t)(p - base) > kNaBytes) return TM_EINVAL;   // layout and array size disagree
@@ -2304,13 +2412,13 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         const Tuning tu = tuning();
         MatchArgs<TT> A;
         A.G = G; A.plans = dplan; A.nq = 1; A.W = W; A.NW = 1; A.F = F; A.d_F = nullptr;
-        A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
+        A.rec = rec; A.excl = excl; A.d_W2 = dW2; A.counter = dctr;
         A.hs_a = nullptr; A.hs_hi = nullptr;
         A.enum_threshold = tu.enum_threshold;
         A.chunk = tu.chunk_items;
         int nsm = sm_count();
         int64_t gl2 = std::min<int64_t>((F + 255) / 256, (int64_t)nsm * 8);
-        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, (int32_t*)len2, lo2, nullptr, nullptr);
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, rec, (int32_t*)len2, nullptr, nullptr);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
@@ -2435,7 +2543,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     int64_t ws2 = scan_dn_ws_elems(Fmax) + 2;
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
                 9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
-                a256(4 * Fs) + (any_hoist ? 4 : 2) * a256(8 * Fs) + a256(8 * (size_t)ws1) + a256(8 * (size_t)ws2) +
+                a256(sizeof(FRec<TT>) * Fs) + (any_hoist ? 3 : 1) * a256(8 * Fs) + a256(8 * (size_t)ws1) +
+                a256(8 * (size_t)ws2) +
                 a256(4 * (Fs / 32 + 1)) + a256(8 * (Fs / 4 + 2)) + a256(4 * Fs) +
                 a256(sizeof(ShiftSums) * (size_t)n_parts);
     cudaError_t e = cudaMalloc(&b->scratch, sz);
@@ -2473,8 +2582,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     int64_t* dF = (int64_t*)take(8);
     int64_t* dW2 = (int64_t*)take(8);
     unsigned long long* dctr = (unsigned long long*)take(8);
-    int32_t* fwin = (int32_t*)take(4 * Fs);
-    int64_t* lo2 = (int64_t*)take(8 * Fs);
+    FRec<TT>* rec = (FRec<TT>*)take(sizeof(FRec<TT>) * Fs);
     int64_t* excl = (int64_t*)take(8 * Fs);
     int32_t* len32 = (int32_t*)take(4 * Fs);
     int64_t* hs_a = any_hoist ? (int64_t*)take(8 * Fs) : nullptr;
@@ -2525,7 +2633,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
     if (rc == TM_OK && Fmax > 0) {
         MatchArgs<TT> A;
         A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = Fmax; A.d_F = dF;
-        A.fwin = fwin; A.lo2 = lo2; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
+        A.rec = rec; A.excl = excl; A.hs_a = hs_a; A.hs_hi = hs_hi;
         A.d_W2 = dW2; A.counter = dctr;
         A.enum_threshold = tu.enum_threshold;
         A.chunk = tu.chunk_items;
@@ -2534,7 +2642,7 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
         k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
             W.fbase, NW, Fmax, dF, bwin);
         count_launch();
-        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, fwin, len32, lo2, hs_a, hs_hi); count_launch();
+        k_level2<TT><<<(unsigned)std::max<int64_t>(gl2, 1), 256, match_smem_bytes(A.nq, 256), st>>>(A, rec, len32, hs_a, hs_hi); count_launch();
         fail(cudaGetLastError(), "k_level2");
         if (rc == TM_OK) rc = scan_lengths(len32, excl, Fmax, dF, dW2, wsp2, ws2, st);
         if (rc == TM_OK) {

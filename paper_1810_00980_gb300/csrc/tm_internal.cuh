@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -326,6 +327,20 @@ void store_profile_batch(double windows_ms, double level2_ms, double match_ms, d
                          double scan_ms);
 void store_profile_graph(double graph_ms);
 void count_launch(int n = 1);
+
+// NVTX ranges naming the host-side phases of a call (graph build, window partition, second-edge
+// ranges, matcher, fold), one after another, so that a profiler can select them (for example
+// ncu --nvtx --nvtx-include "tm_match/"); without a tool attached each call costs a branch
+struct NvtxPhases {
+    nvtxRangeId_t id = 0;
+    bool open = false;
+    void next(const char* name) {
+        if (open) nvtxRangeEnd(id);
+        open = name != nullptr;
+        if (open) id = nvtxRangeStartA(name);
+    }
+    ~NvtxPhases() { next(nullptr); }
+};
 
 // CUDA events on a stream, created only while profiling is on
 struct PhaseEvents {
