@@ -718,7 +718,7 @@ __global__ void k_chunkf(const int64_t* __restrict__ excl, int64_t Fh, const int
 
 // one warp-uniform grid-stride loop over first edges f
 template <typename TT>
-__global__ void __launch_bounds__(256, 5) k_level2(MatchArgs<TT> A, FRec<TT>* __restrict__ rec,
+__global__ void __launch_bounds__(256, 8) k_level2(MatchArgs<TT> A, FRec<TT>* __restrict__ rec,
                                                 int32_t* __restrict__ len2, int64_t* __restrict__ hs_a,
                                                 int64_t* __restrict__ hs_hi) {
     const GraphDevT<TT>& G = A.G;
