@@ -322,6 +322,25 @@ int tm_profile_enable(int32_t on);
 int tm_release_cached_memory(void);
 int tm_profile_last(tm_profile* out);
 
+/* ---- bounds-checked build ------------------------------------------------------
+ * The paper has no counterpart: this is a debugging aid.  The library is also built as
+ * libtmotif_checked.so (compiled with TM_CHECKED), where every index the kernels derive
+ * from data -- work items, first edges, adjacency candidates, windows, query indices,
+ * node ids into the offset arrays, pair segments, sort and offset positions -- is
+ * checked against the size of the array it indexes.  A failed check sets one bit of a
+ * device error word and redirects the access to element 0 of that array (no access
+ * outside it, no trap), so the call completes and its results are unreliable.
+ *   tm_check_status   *word = the OR of the bits set since the last clear:
+ *                     1 work item or first edge, 2 window or query, 4 view position,
+ *                     8 node id, 16 candidate or pair range, 32 sort or offset position,
+ *                     64 the self-test; clear != 0 resets them.  Synchronous.
+ *   tm_check_selftest runs one deliberately out-of-range index (one past a one-element
+ *                     device array) through the check, which reads element 0 and sets
+ *                     bit 64, so that a test can see the mechanism work.
+ * In the ordinary build both return TM_EINVAL (*word = 0). */
+int tm_check_status(uint32_t* word, int32_t clear);
+int tm_check_selftest(void);
+
 /* ---- serving -----------------------------------------------------------------
  * A server keeps graphs resident, accepts queries from any thread, and runs
  * them in continuous batches: queries that arrive while a batch is on the GPU

@@ -309,6 +309,24 @@ int tm_autotune(const tm_graph* g, const tm_query* queries, int32_t n_queries, t
     return TM_OK;
 }
 
+int tm_check_status(uint32_t* word, int32_t clear) {
+    if (!word) { set_error("NULL argument"); return TM_EINVAL; }
+#ifndef TM_CHECKED
+    *word = 0;
+    set_error("bounds checks are not compiled into this build");
+    return TM_EINVAL;
+#else
+    unsigned a = 0, b = 0, c = 0;
+    TM_TRY(check_word_match(&a, clear != 0));
+    TM_TRY(check_word_graph(&b, clear != 0));
+    TM_TRY(check_word_prims(&c, clear != 0));
+    *word = a | b | c;
+    return TM_OK;
+#endif
+}
+
+int tm_check_selftest(void) { return check_selftest(); }
+
 int tm_profile_enable(int32_t on) {
     g_prof_on.store(on != 0);
     return TM_OK;

@@ -70,7 +70,7 @@ __global__ void k_offsets(const uint32_t* __restrict__ keys, int64_t m, int32_t 
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t prev = i == 0 ? -1 : (int64_t)keys[i - 1];
         int64_t cur = i == m ? (int64_t)n : (int64_t)keys[i];
-        for (int64_t v = prev + 1; v <= cur; v++) off[v] = i;
+        for (int64_t v = prev + 1; v <= cur; v++) off[TM_CHK_IDX(v, (int64_t)n + 1, kChkNode)] = i;
     }
 }
 
@@ -691,3 +691,7 @@ int tm_graph_get_info(const tm_graph* g, tm_graph_info* info) {
 }
 
 }  // extern "C"
+
+namespace tmo {
+TM_DEFINE_CHECK_WORD(check_word_graph)
+}  // namespace tmo

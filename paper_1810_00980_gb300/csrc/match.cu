@@ -177,10 +177,10 @@ __device__ __forceinline__ void level_range(const GraphDevT<TT>& G, const LevelP
         ta = G.pair_t;
         if (!pair_segment(G, phi_get(phi, P.su), phi_get(phi, P.sv), a, b)) return;
     } else if (P.view == kOut) {
-        int32_t u = phi_get(phi, P.su);
+        int32_t u = (int32_t)TM_CHK_IDX(phi_get(phi, P.su), G.n, kChkNode);
         ta = G.out_t; a = __ldg(G.out_off + u); b = __ldg(G.out_off + u + 1);
     } else if (P.view == kIn) {
-        int32_t v = phi_get(phi, P.sv);
+        int32_t v = (int32_t)TM_CHK_IDX(phi_get(phi, P.sv), G.n, kChkNode);
         ta = G.in_t; a = __ldg(G.in_off + v); b = __ldg(G.in_off + v + 1);
     } else {
         ta = G.t; a = 0; b = G.m;
@@ -775,12 +775,16 @@ __global__ void __launch_bounds__(256, 8) k_level2(MatchArgs<TT> A, FRec<TT>* __
             if (valid) acc.win = wi;
         }
         if (!valid) continue;
-        const QPlan& Q = PL[A.W.q[wi]];
+        wi = TM_CHK_IDX(wi, A.NW, kChkWindow);
+        const QPlan& Q = PL[TM_CHK_IDX(A.W.q[wi], A.nq, kChkWindow)];
         int64_t e1 = A.W.lo[wi] + (f - A.W.fbase[wi]);
-        if (Q.full) e1 = __ldg(Q.perm + e1);
+        if (Q.full) e1 = __ldg(Q.perm + TM_CHK_IDX(e1, (int64_t)Q.b * G.m, kChkView));
+        e1 = TM_CHK_IDX(e1, G.m, kChkView);
         int32_t s1, d1;
         int64_t t1;
         first_edge(G, Q.order, e1, s1, d1, t1);
+        s1 = (int32_t)TM_CHK_IDX(s1, G.n, kChkNode);
+        d1 = (int32_t)TM_CHK_IDX(d1, G.n, kChkNode);
         int64_t thi = first_thi(Q, A.W, wi, t1);
         int64_t len = 0, lo = 0, ha = 0, hh = 0;
         // a segment of a streamed graph owns the exact queries' first edges in [own_lo, own_hi)
@@ -933,6 +937,8 @@ __global__ void __launch_bounds__(256, 8) k_level2(MatchArgs<TT> A, FRec<TT>* __
                 }
             }
         }
+        // (closing-side items, lo < 0, are checked where k_match decodes them)
+        TM_CHK(len <= 0 || lo < 0 || lo + len <= G.m, kChkRange);
         len2[f] = (int32_t)len;   // a range inside one view: below 2^31
         if (len > 0) {            // the matcher reads these only for first edges with items
             FRec<TT> r;
@@ -1050,7 +1056,7 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
                 const LevelPlan L = Q.lv[Q.l - 1];
                 int xl = P.bind_u ? P.su : P.sv;
                 bool x_src = L.su == xl;
-                int64_t c = olo + (x - ost);
+                int64_t c = TM_CHK_IDX(olo + (x - ost), G.m, kChkView);
                 int32_t xv = x_src ? __ldg(G.in_nbr + c) : __ldg(G.out_nbr + c);
                 int64_t tl = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
                 acc.s(A_CAND) += 1;
@@ -1066,7 +1072,7 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
                 }
             } else {
                 int32_t s, d;
-                read_cand(G, P, ophi, olo + (x - ost), s, d, tc);
+                read_cand(G, P, ophi, TM_CHK_IDX(olo + (x - ost), G.m, kChkView), s, d, tc);
                 ok = check_bind(P, ophi, s, d);
                 if (D == Q.l - 1) {
                     acc.s(A_INST) += 1;
@@ -1163,10 +1169,10 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
             for (int i = 0; i < KMAX; i++) phi[i] = -1;
             bool deeper = false;
             if (valid) {
-                int64_t f = fw;
+                int64_t f = TM_CHK_IDX(fw, F, kChkQueue);
                 const FRec<TT> r = A.rec[f];
-                win = r.win;
-                q = r.q;
+                win = TM_CHK_IDX(r.win, A.NW, kChkWindow);
+                q = (int32_t)TM_CHK_IDX(r.q, A.nq, kChkWindow);
                 const QPlan& Q = PL[q];
                 phi[0] = r.s1;
                 phi[1] = r.d1;
@@ -1178,7 +1184,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     // (middle-pair edges before t_j) - (those at or before t1)
                     const bool mid_rev = Q.ex23 & kEx23MidRev, last_rev = Q.ex23 & kEx23LastRev;
                     const int64_t* S = mid_rev == last_rev ? G.ex_own : G.ex_rev;
-                    int64_t j = A.hs_a[f] + (w - A.excl[f]);
+                    int64_t j = TM_CHK_IDX(A.hs_a[f] + (w - A.excl[f]), G.m, kChkView);
                     int64_t t3 = __ldg(G.pair_t + j);
                     int64_t cnt = (__ldg(S + j + 1) - __ldg(S + j)) - A.hs_hi[f];
                     if (Q.mode == TM_MODE_EXACT) {
@@ -1199,7 +1205,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     const LevelPlan L = Q.lv[2];
                     const LevelPlan M1 = Q.lv[1];
                     int64_t lo1 = -1 - l2, end1 = A.hs_hi[f], ha0 = A.hs_a[f];
-                    int64_t p3 = ha0 + (w - A.excl[f]);
+                    int64_t p3 = TM_CHK_IDX(ha0 + (w - A.excl[f]), G.m, kChkView);
                     int64_t t3 = __ldg(G.pair_t + p3);
                     acc_switch(acc, win, A.W.acc);
                     acc.s(A_CAND) += 1;
@@ -1239,7 +1245,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                 if (l2 < 0) {
                     const LevelPlan L = Q.lv[2];
                     const LevelPlan M1 = Q.lv[1];
-                    int64_t c = (-1 - l2) + (w - A.excl[f]);
+                    int64_t c = TM_CHK_IDX((-1 - l2) + (w - A.excl[f]), G.m, kChkView);
                     bool x_src = L.su == 2;
                     int32_t x = x_src ? __ldg(G.in_nbr + c) : __ldg(G.out_nbr + c);
                     t3 = x_src ? __ldg(G.in_t + c) : __ldg(G.out_t + c);
@@ -1253,7 +1259,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                 } else {
                     const LevelPlan P = Q.lv[1];
                     int32_t s, d;
-                    read_cand(G, P, phi, l2 + (w - A.excl[f]), s, d, tc);
+                    read_cand(G, P, phi, TM_CHK_IDX(l2 + (w - A.excl[f]), G.m, kChkView), s, d, tc);
                     ok = check_bind(P, phi, s, d);
                     if (Q.hoist) {
                         ha = A.hs_a[f];
@@ -2283,6 +2289,38 @@ int count_plain(const tm_graph* g, const tm_motif* m, int64_t delta, int64_t* co
     if (g && g->dev.tbytes == 4) return count_plain_t<int32_t>(g, m, delta, count);
     return count_plain_t<int64_t>(g, m, delta, count);
 }
+
+TM_DEFINE_CHECK_WORD(check_word_match)
+
+#ifdef TM_CHECKED
+namespace {
+// one out-of-range index (n for an array of n elements) through the checked accessor: the
+// check records it and the read goes to element 0
+__global__ void k_check_selftest(const int64_t* __restrict__ a, int64_t n, int64_t* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = a[TM_CHK_IDX(n, n, kChkSelf)];
+}
+}  // namespace
+
+int check_selftest() {
+    int64_t* d = nullptr;
+    TM_CUDA(cudaMalloc(&d, 2 * sizeof(int64_t)));
+    cudaError_t e = cudaMemset(d, 0, 2 * sizeof(int64_t));
+    if (e == cudaSuccess) {
+        k_check_selftest<<<1, 32>>>(d, 1, d + 1);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(e, "tm_check_selftest", __FILE__, __LINE__);
+    return TM_OK;
+}
+#else
+int check_selftest() {
+    set_error("bounds checks are not compiled into this build");
+    return TM_EINVAL;
+}
+#endif
 
 }  // namespace tmo
 

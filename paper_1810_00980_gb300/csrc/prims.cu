@@ -355,7 +355,7 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const V* __restrict__ vin,
     int64_t tn = min((int64_t)kSortTile, n - tbase);
     for (int i = threadIdx.x; i < tn; i += blockDim.x) {
         uint32_t k = skey[i];
-        int64_t pos = gbase[(k >> shift) & mask] + i;
+        int64_t pos = TM_CHK_IDX(gbase[(k >> shift) & mask] + i, n, kChkSort);
         kout[pos] = k;
         vout[pos] = sval[i];
     }
@@ -705,4 +705,8 @@ int sm_count() {
     return n;
 }
 
+}  // namespace tmo
+
+namespace tmo {
+TM_DEFINE_CHECK_WORD(check_word_prims)
 }  // namespace tmo

@@ -15,6 +15,57 @@ constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 // ----------------------------------------------------------------------------
+// bounds-checked build
+// ----------------------------------------------------------------------------
+// Compiled with -DTM_CHECKED (libtmotif_checked.so), the indices the kernels derive from data
+// (work items, first edges, candidates, windows, pair segments, sort positions) are checked
+// against the sizes of the arrays they index.  A failed check sets its bit in the
+// translation unit's device error word and the access goes to element 0 instead, so the
+// kernel never touches memory outside its arrays and runs to the end; the host reads and
+// clears the words with tm_check_status.  Without TM_CHECKED the checks compile to nothing.
+enum CheckBit : unsigned {
+    kChkQueue = 1u,     // work item / first edge beyond the batch's counts
+    kChkWindow = 2u,    // window slot or query index beyond the batch's tables
+    kChkView = 4u,      // position beyond an adjacency view (m entries)
+    kChkNode = 8u,      // node id beyond n (offsets arrays hold n + 1 entries)
+    kChkRange = 16u,    // a candidate or pair range not inside [0, m]
+    kChkSort = 32u,     // a sort or scan output position beyond its array
+    kChkSelf = 64u,     // the self-test's deliberate out-of-range index
+};
+#ifdef TM_CHECKED
+static __device__ unsigned int g_tm_check_word;   // one per translation unit
+__device__ __forceinline__ int64_t chk_idx(int64_t i, int64_t n, unsigned bit) {
+    if ((unsigned long long)i >= (unsigned long long)n) {
+        atomicOr(&g_tm_check_word, bit);
+        return 0;
+    }
+    return i;
+}
+#define TM_CHK_IDX(i, n, bit) ::tmo::chk_idx((int64_t)(i), (int64_t)(n), (bit))
+#define TM_CHK(cond, bit) \
+    do { if (!(cond)) atomicOr(&::tmo::g_tm_check_word, (bit)); } while (0)
+// the translation unit's error word, read (and cleared) from the host
+#define TM_DEFINE_CHECK_WORD(fn)                                                             \
+    int fn(unsigned* w, bool clear) {                                                        \
+        if (cudaMemcpyFromSymbol(w, ::tmo::g_tm_check_word, sizeof(unsigned)) != cudaSuccess) \
+            return TM_ECUDA;                                                                 \
+        unsigned z = 0;                                                                      \
+        if (clear && cudaMemcpyToSymbol(::tmo::g_tm_check_word, &z, sizeof(unsigned)) != cudaSuccess) \
+            return TM_ECUDA;                                                                 \
+        return TM_OK;                                                                        \
+    }
+#else
+#define TM_CHK_IDX(i, n, bit) (i)
+#define TM_CHK(cond, bit) do {} while (0)
+#define TM_DEFINE_CHECK_WORD(fn) \
+    int fn(unsigned* w, bool) { *w = 0; return TM_OK; }
+#endif
+int check_word_match(unsigned* w, bool clear);
+int check_word_graph(unsigned* w, bool clear);
+int check_word_prims(unsigned* w, bool clear);
+int check_selftest();
+
+// ----------------------------------------------------------------------------
 // error plumbing
 // ----------------------------------------------------------------------------
 void set_error(const std::string& msg);
@@ -436,6 +487,10 @@ __device__ __forceinline__ bool pair_segment(const GraphDevT<TT>& G, int32_t u, 
         if (sl.x == key) {
             a = (int64_t)(uint32_t)sl.y;
             b = a + (int64_t)(sl.y >> 32);
+            TM_CHK(b <= G.m, kChkRange);
+#ifdef TM_CHECKED
+            if (b > G.m) a = b = 0;   // an empty segment instead of one beyond the view
+#endif
             return true;
         }
         unsigned long long k = sl.x;

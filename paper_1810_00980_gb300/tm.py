@@ -16,7 +16,9 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libtmotif.so")
+# TMOTIF_CHECKED=1 selects the bounds-checked build (libtmotif_checked.so; see tm_check_status)
+LIB_PATH = os.path.join(HERE, "_build", "libtmotif_checked.so" if os.environ.get("TMOTIF_CHECKED") == "1"
+                        else "libtmotif.so")
 
 TM_OK, TM_EINVAL, TM_EUNSORTED, TM_ERANGE, TM_ENOMEM, TM_EADMIT, TM_ETIMEOUT = range(7)
 TM_ESTACK, TM_EOVERFLOW, TM_ECUDA, TM_PENDING, TM_ENOTFOUND, TM_ECANCELLED, TM_ESHUTDOWN = range(7, 14)
@@ -106,6 +108,8 @@ _SIGS = {
     "tm_profile_enable": (ctypes.c_int, [_c_i32]),
     "tm_profile_last": (ctypes.c_int, [_vp]),
     "tm_release_cached_memory": (ctypes.c_int, []),
+    "tm_check_status": (ctypes.c_int, [_vp, _c_i32]),
+    "tm_check_selftest": (ctypes.c_int, []),
     "tm_serve_create": (ctypes.c_int, [_vp, _vp]),
     "tm_serve_attach_graph": (ctypes.c_int, [_vp, _vp, _vp]),
     "tm_serve_submit": (ctypes.c_int, [_vp, _c_i32, _vp, _vp]),
@@ -130,6 +134,19 @@ def lib():
             fn.argtypes = args
         _LIB = L
     return _LIB
+
+
+def check_status(clear: bool = True) -> int:
+    """tm_check_status: the bits of the failed bounds checks since the last clear (checked
+    build only; the ordinary build raises TmError(TM_EINVAL))."""
+    w = ctypes.c_uint32(0)
+    _check(lib().tm_check_status(ctypes.byref(w), 1 if clear else 0), "tm_check_status")
+    return w.value
+
+
+def check_selftest():
+    """tm_check_selftest: one deliberately out-of-range index through the checks."""
+    _check(lib().tm_check_selftest(), "tm_check_selftest")
 
 
 def _check(status: int, where: str):
