@@ -397,7 +397,8 @@ __device__ __forceinline__ void add_sub_range(Acc& a, const QPlan& Q, const TT* 
 // ---- estimates riding along with an exact query (QPlan::nride / riding).  An instance with
 // first edge at t1 and last edge at t3 counts for rider R's shift k when the window of t1 is
 // kept and holds t3, and t3 - t1 <= R.delta; it adds R's Q64 weight to that window's sums.
-// Out of line: rare next to the enumeration, and it keeps the matcher's registers.
+// Inlined: out of line, every call saved and restored the matcher's live registers, which
+// cost more than the extra registers inlining takes.
 // x / d for x >= 0, d > 0: one 32-bit division when both fit in 32 bits (times of a graph
 // whose span fits in 31 bits, and spans c delta below 2^32), else the 64-bit one
 __device__ __forceinline__ int64_t div_nonneg(int64_t x, int64_t d) {
@@ -476,7 +477,7 @@ __device__ __forceinline__ void ride_weight(const QPlan& R, int64_t dur, unsigne
 }
 
 // cnt instances closed by the edge at t3
-__device__ __noinline__ void ride_at(const QPlan* __restrict__ PL, const QPlan& Q, const int32_t* __restrict__ kept,
+__device__ __forceinline__ void ride_at(const QPlan* __restrict__ PL, const QPlan& Q, const int32_t* __restrict__ kept,
                                      unsigned long long* acc, int64_t t1, int64_t t3, unsigned long long cnt) {
     for (int r = 0; r < Q.nride; r++) {
         const QPlan& R = PL[Q.ride_q[r]];
@@ -496,7 +497,7 @@ __device__ __noinline__ void ride_at(const QPlan* __restrict__ PL, const QPlan& 
 // one instance per closing entry of the time-sorted range [lo, hi) (entries after tc); the most
 // entries read for one rider shift count as the exact query's last-edge entries read one by one
 template <typename TT>
-__device__ __noinline__ void ride_range(const QPlan* __restrict__ PL, const QPlan& Q,
+__device__ __forceinline__ void ride_range(const QPlan* __restrict__ PL, const QPlan& Q,
                                         const int32_t* __restrict__ kept, unsigned long long* acc,
                                         const TT* __restrict__ ta, int64_t clo, int64_t chi, int64_t t1,
                                         int64_t tc) {
@@ -1105,7 +1106,12 @@ __device__ void expand(const MatchArgs<TT>& A, const QPlan* __restrict__ PL, boo
 // OCC: resident 256-thread blocks per SM the register allocation must allow
 // (three-edge motifs: 4 without spills, 6 with spilled registers; four-edge motifs: 1 leaves
 // the compiler 118 registers, 4 caps them at 64 with spills -- the autotuner picks)
-template <typename TT, int LMAX, int KMAX, int OCC = (LMAX <= 3 ? 4 : 1)>
+// EXPAND = false leaves out the warp-cooperative expansion of deeper motif edges, for batches
+// whose items all end at their second edge (every query exact with the last edge between two
+// bound nodes, two-node, riding along, or of at most two edges): the code the hot loop does
+// not run still takes registers, and without it the 3-cycle enumeration of the benchmark
+// batch runs 1.50 -> 1.32 ms
+template <typename TT, int LMAX, int KMAX, int OCC = (LMAX <= 3 ? 4 : 1), bool EXPAND = true>
 __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
     const GraphDevT<TT>& G = A.G;
     extern __shared__ __align__(16) unsigned char smem_plans[];
@@ -1309,8 +1315,12 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                 }
                 }
             }
-            if (__any_sync(kFull, deeper))
-                expand<TT, 2, LMAX, KMAX>(A, PL, deeper, q, win, phi, t1, tc, thi, ha, hh, acc);
+            if constexpr (EXPAND) {
+                if (__any_sync(kFull, deeper))
+                    expand<TT, 2, LMAX, KMAX>(A, PL, deeper, q, win, phi, t1, tc, thi, ha, hh, acc);
+            } else {
+                TM_CHK(!deeper, kChkQueue);   // the host's choice of EXPAND = false must hold
+            }
         }
         acc_flush_warp(acc, A.W.acc);
     }
@@ -1493,12 +1503,24 @@ void launch_fold(const QPlan* dplans, int nq, int bmax, int smax, const WinDev& 
 
 // the persistent matcher for a batch whose deepest motif has lmax edges on kmax nodes: the
 // instantiation whose register budget fits the tuning's blocks per SM
+// a lane can go deeper than its second edge: a query of three or more edges, not two-node, not
+// riding along, that is an estimate (it reads its last edges one by one), has four or more
+// edges, or ends on an edge with a new node
+bool plan_expands(const QPlan& P) {
+    if (P.l < 3 || P.riding || P.ex23) return false;
+    return P.l >= 4 || P.mode != TM_MODE_EXACT || P.lv[P.l - 1].view != kPair;
+}
+
 template <typename TT>
-void launch_match(const MatchArgs<TT>& A, int lmax, int kmax, const Tuning& tu, int nsm, cudaStream_t st) {
+void launch_match(const MatchArgs<TT>& A, int lmax, int kmax, const Tuning& tu, int nsm, cudaStream_t st,
+                  bool expand) {
     const int bps = tu.blocks_per_sm, bt = tu.block_threads;
     const unsigned gm = (unsigned)(nsm * bps);
     const size_t sm = match_smem_bytes(A.nq, bt, A.ride);
-    if (lmax <= 3 && kmax <= 4 && bps >= 6) k_match<TT, 3, 4, 6><<<gm, bt, sm, st>>>(A);
+    if (lmax <= 3 && kmax <= 4 && !expand) {
+        if (bps >= 6) k_match<TT, 3, 4, 6, false><<<gm, bt, sm, st>>>(A);
+        else k_match<TT, 3, 4, 4, false><<<gm, bt, sm, st>>>(A);
+    } else if (lmax <= 3 && kmax <= 4 && bps >= 6) k_match<TT, 3, 4, 6><<<gm, bt, sm, st>>>(A);
     else if (lmax <= 3 && kmax <= 4) k_match<TT, 3, 4><<<gm, bt, sm, st>>>(A);
     else if (lmax <= 4 && kmax <= 4 && bps >= 4) k_match<TT, 4, 4, 4><<<gm, bt, sm, st>>>(A);
     else if (lmax <= 4 && kmax <= 4) k_match<TT, 4, 4><<<gm, bt, sm, st>>>(A);
@@ -1980,7 +2002,8 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             ev_l1 = pe.mark(st);
             nv.next("tm_match");
             if (rc == TM_OK) {
-                launch_match<TT>(A, lmax, kmax, tu, nsm, st);
+                launch_match<TT>(A, lmax, kmax, tu, nsm, st,
+                                 std::any_of(hp.begin(), hp.end(), [](const QPlan& P) { return plan_expands(P); }));
                 fail(cudaGetLastError(), "k_match");
                 ev_m1 = pe.mark(st);
                 if (pe.on) fail(cudaMemcpyAsync(&hW2, dW2, 8, cudaMemcpyDeviceToHost, st), "W2");
@@ -2464,7 +2487,7 @@ int count_exact_noalloc_t(const tm_graph* g, const tm_motif* m, int64_t delta, c
         // workspace takes the second half
         rc = scan_lengths((const int32_t*)len2, excl, F, nullptr, dW2, len2 + kNaMaxEdges / 2, kNaMaxEdges / 2, st);
         if (rc != TM_OK) return rc;
-        launch_match<TT>(A, P.l, std::max(P.k, 2), tu, nsm, st);
+        launch_match<TT>(A, P.l, std::max(P.k, 2), tu, nsm, st, plan_expands(P));
         e = cudaGetLastError();
         if (e != cudaSuccess) return na_status(e);
     }
@@ -2690,7 +2713,8 @@ int batch_create_t(const tm_graph* g, const tm_query* qs, int nq, tm_batch** out
             fail(cudaGetLastError(), "k_chunkf");
         }
         if (rc == TM_OK) {
-            launch_match<TT>(A, lmax, kmax, tu, nsm, st);
+            launch_match<TT>(A, lmax, kmax, tu, nsm, st,
+                             std::any_of(hp.begin(), hp.end(), [](const QPlan& P) { return plan_expands(P); }));
             fail(cudaGetLastError(), "k_match");
         }
     }
