@@ -255,6 +255,29 @@ int bits_for(int32_t n) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// A second stream of the calling thread on device dev, with two events, for the in-view sort
+// that runs beside the out-view sort (null when it cannot be created: the sorts then share st)
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream* side_stream(int dev) {
+    constexpr int kDevs = 64;
+    thread_local SideStream ss[kDevs];
+    if (dev < 0 || dev >= kDevs) return nullptr;
+    SideStream& x = ss[dev];
+    if (!x.s) {
+        if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            x.s = nullptr;
+            return nullptr;
+        }
+    }
+    return &x;
+}
+
 int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, int64_t m,
                 int32_t n_nodes, cudaStream_t st, tm_graph** out) {
     if (!out) { set_error("out is NULL"); return TM_EINVAL; }
@@ -369,7 +392,11 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
     uint32_t *ks, *kd, *va, *vb, *kt, *vt;
     int64_t *head, *pid, *dP;
     // index path: 6 u32 + 2 i64 per edge; payload path (32-bit times): 3 u32 + 3 u64
-    size_t scratch = std::max(6 * align256(4 * M) + 2 * sz_i64m, 3 * align256(4 * M) + 3 * sz_i64m) + 256;
+    // (the payload path takes a fourth key and value array when the in-view sort runs on a side
+    // stream beside the out-view sort)
+    SideStream* side = tb == 4 ? side_stream(dev) : nullptr;
+    const int kv = side ? 4 : 3;
+    size_t scratch = std::max(6 * align256(4 * M) + 2 * sz_i64m, kv * align256(4 * M) + kv * sz_i64m) + 256;
     ScratchLease lease;
     int lrc = scratch_acquire(scratch, st, lease);
     if (lrc != TM_OK) {
@@ -416,14 +443,36 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
         uint32_t* k0 = (uint32_t*)take2(4 * M);
         uint32_t* k1 = (uint32_t*)take2(4 * M);
         uint32_t* k2 = (uint32_t*)take2(4 * M);
+        uint32_t* k3 = side ? (uint32_t*)take2(4 * M) : k0;
         uint64_t* p0 = (uint64_t*)take2(8 * M);
         uint64_t* p1 = (uint64_t*)take2(8 * M);
         uint64_t* p2 = (uint64_t*)take2(8 * M);
+        uint64_t* p3 = side ? (uint64_t*)take2(8 * M) : p0;
         uint32_t* kr = nullptr;
         uint64_t* pr = nullptr;
         k_ingest_kv<<<gr, kThreads, 0, st>>>(d_src, d_dst, d_t, m, tmin, gs, gd, (int32_t*)gt, k0, k1, p0, p1);
         count_launch();
         if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+        // in view: (destination; source | time) stably sorted by destination -- on the side
+        // stream when there is one, beside the out view's sort
+        cudaStream_t sin = side ? side->s : st;
+        if (rc == TM_OK && side && (cudaEventRecord(side->fork, st) != cudaSuccess ||
+                                    cudaStreamWaitEvent(sin, side->fork, 0) != cudaSuccess))
+            rc = TM_ECUDA;
+        uint32_t* kr_in = nullptr;
+        uint64_t* pr_in = nullptr;
+        auto in_view = [&]() {
+            if (rc == TM_OK) rc = radix_sort_kv64(k1, p1, k3, p3, m, bits, sin, &kr_in, &pr_in);
+            if (rc == TM_OK) {
+                k_offsets<<<grid_for(m + 1), kThreads, 0, sin>>>(kr_in, m, n, in_off); count_launch();
+                k_split_view<<<gr, kThreads, 0, sin>>>(pr_in, m, in_nbr, (int32_t*)in_t); count_launch();
+                if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+                if (rc == TM_OK && cudaMemcpyAsync(in_dst, kr_in, 4 * M, cudaMemcpyDeviceToDevice, sin) != cudaSuccess)
+                    rc = TM_ECUDA;
+            }
+            if (side && cudaEventRecord(side->join, sin) != cudaSuccess && rc == TM_OK) rc = TM_ECUDA;
+        };
+        if (side) in_view();
         // out view: (source; destination | time) stably sorted by source
         if (rc == TM_OK) rc = radix_sort_kv64(k0, p0, k2, p2, m, bits, st, &kr, &pr);
         if (rc == TM_OK) {
@@ -433,14 +482,11 @@ int build_graph(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t, 
             if (rc == TM_OK && cudaMemcpyAsync(out_src, kr, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 rc = TM_ECUDA;
         }
-        // in view: (destination; source | time) stably sorted by destination
-        if (rc == TM_OK) rc = radix_sort_kv64(k1, p1, k0, p0, m, bits, st, &kr, &pr);
-        if (rc == TM_OK) {
-            k_offsets<<<grid_for(m + 1), kThreads, 0, st>>>(kr, m, n, in_off); count_launch();
-            k_split_view<<<gr, kThreads, 0, st>>>(pr, m, in_nbr, (int32_t*)in_t); count_launch();
-            if (cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
-            if (rc == TM_OK && cudaMemcpyAsync(in_dst, kr, 4 * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-                rc = TM_ECUDA;
+        if (side) {
+            // the pair view needs the in view, and reuses the in-view sort's arrays
+            if (cudaStreamWaitEvent(st, side->join, 0) != cudaSuccess && rc == TM_OK) rc = TM_ECUDA;
+        } else {
+            in_view();   // after the out view, in its arrays (k0 / p0 are free again)
         }
         // pair view: the in view stably re-sorted by source = (source, destination, time)
         if (rc == TM_OK) {

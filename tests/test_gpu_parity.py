@@ -724,7 +724,7 @@ def test_estimates_ride_along_exact_queries(tm, orc):
         want += [("exact", orc.count_exact(src, dst, t, ms, md, 86400, threads=8)),
                  ("exact", orc.count_exact(src, dst, t, ms, md, 3600, threads=8))]
         for (d, c, p, seed, b) in ((86400, 30, 1.0, 3, 1), (3600, 10, 1.0, 4, 1), (600, 5, 1.0, 5, 1),
-                                   (3600, 10, 0.3, 6, 2), (600, 5, 0.5, 7, 1)):
+                                   (3600, 10, 0.3, 6, 2), (600, 5, 0.5, 7, 1), (3600, 4, 1.0, 9, 2)):
             qs.append(tm.estimate_query(mo, d, c, p, seed, b=b))
             want.append(("est", orc.estimate(src, dst, t, ms, md, d, c, p, seed, b=b, threads=8)))
         qs.append(tm.estimate_query(mo, 3600, 5, 20.0, 8, q_mode=tm.TM_Q_EDGES))
