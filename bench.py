@@ -76,6 +76,22 @@ def whole_job_rate(units_per_step: int, steps: int, world: int, total_ms: float)
     return world * units_per_step * steps / (total_ms / 1e3)
 
 
+def kernel_bytes(qs, results):
+    """Algorithmic bytes of the matcher kernels for one batch, from the kernels' own counters.
+    k_match: each second-edge candidate read (12 B), two boundary timestamps per range-counted
+    closing (16 B), and each last-edge entry that an estimate reads one by one (8 B).  k_ride
+    (the deferred pass of riders and smaller spans): the closing entries it reads one by one for
+    the riders (8 B each, counted on the exact query they ride on).  k_level2: the first edge
+    read once (16 B), and beside it the implementation's bytes (the two range-boundary
+    timestamps 16 B and the 20 B it writes per first edge)."""
+    exact = [getattr(q, "mode", 0) == 0 for q in qs]
+    i_ride = sum(r["inst_read"] for r, e in zip(results, exact) if e)
+    i_est = sum(r["inst_read"] for r, e in zip(results, exact) if not e)
+    f = sum(r["first_edges"] for r in results)
+    return {"k_match": sum(12 * r["cand_edges"] + 16 * r["last_ranges"] for r in results) + 8 * i_est,
+            "k_ride": 8 * i_ride, "k_level2": 16 * f, "k_level2_impl": (16 + 16 + 20) * f}
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -561,7 +577,7 @@ def bursty_100m_4cycle(tm, torch, steps, warmup, world=1, on_device=False):
     total_ms = e0.elapsed_time(e1)
     results = b.results()
     launches = tm.profile_last()["launches"] - launches0
-    b_match = sum(12 * r["cand_edges"] + 16 * r["last_ranges"] + 8 * r["inst_read"] for r in results)
+    b_match = kernel_bytes(qs, results)["k_match"]
     mm = statistics.median(match_ms)
     hbm = peaks().get("hbm_gbs") or 6800.0
     achieved = b_match / (mm / 1e3) / 1e9 if mm > 0 else 0.0
@@ -658,8 +674,8 @@ def run_hubs_1b_outstar(args, tm, torch, world, rank):
     launches = tm.profile_last()["launches"] - launches0
     mm = statistics.median(p["match_ms"] for p in prof)
     ml = statistics.median(p["level2_ms"] for p in prof)
-    b_match = sum(12 * r["cand_edges"] + 16 * r["last_ranges"] + 8 * r["inst_read"] for r in results)
-    b_level2 = sum((16 + 16 + 20) * r["first_edges"] for r in results)
+    kbytes = kernel_bytes(qs, results)
+    b_match, b_level2 = kbytes["k_match"], kbytes["k_level2"]
     dominant = "k_level2" if ml > mm else "k_match"
     kb, kms = (b_level2, ml) if dominant == "k_level2" else (b_match, mm)
     hbm = peaks().get("hbm_gbs") or 6800.0
@@ -919,14 +935,11 @@ def main():
     hbm = pk.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    # algorithmic bytes: k_match reads each candidate (12 B), two boundary timestamps per
-    # range-counted closing (16 B) and each last-edge entry read one by one (8 B);
-    # k_level2 reads each first edge (16 B) and its range boundaries (16 B), and writes
-    # its per-first-edge record (window 4 B, range start 8 B, length 8 B)
-    b_match = sum(12 * r["cand_edges"] + 16 * r["last_ranges"] + 8 * r["inst_read"] for r in results)
-    b_level2 = sum((16 + 16 + 20) * r["first_edges"] for r in results)
+    kbytes = kernel_bytes(qs, results)
+    b_match, b_level2 = kbytes["k_match"], kbytes["k_level2"]
     mm = statistics.median(match_ms) if match_ms else float("nan")
     ml = statistics.median(level2_ms) if level2_ms else float("nan")
+    mr = statistics.median(p["ride_ms"] for p in prof) if prof else float("nan")
     dominant = "k_level2" if ml > mm else "k_match"
     kb, kms = (b_level2, ml) if dominant == "k_level2" else (b_match, mm)
     achieved = kb / (kms / 1e3) / 1e9 if kms and kms > 0 else 0.0
@@ -945,8 +958,13 @@ def main():
             traffic = None
     other = {"k_match": {"ms": mm, "algorithmic_bytes": b_match,
                          "achieved_gbs": b_match / (mm / 1e3) / 1e9 if mm > 0 else 0.0},
+             "k_ride": {"ms": mr, "algorithmic_bytes": kbytes["k_ride"],
+                        "achieved_gbs": kbytes["k_ride"] / (mr / 1e3) / 1e9 if mr > 0 else 0.0,
+                        "records": prof[-1].get("ride_records") if prof else None},
              "k_level2": {"ms": ml, "algorithmic_bytes": b_level2,
-                          "achieved_gbs": b_level2 / (ml / 1e3) / 1e9 if ml > 0 else 0.0}}
+                          "achieved_gbs": b_level2 / (ml / 1e3) / 1e9 if ml > 0 else 0.0,
+                          "implementation_bytes": kbytes["k_level2_impl"],
+                          "implementation_gbs": kbytes["k_level2_impl"] / (ml / 1e3) / 1e9 if ml > 0 else 0.0}}
 
     if rank != 0:
         if world > 1:
@@ -971,7 +989,8 @@ def main():
         "plain_exact_queries_per_s": plain_qps,
         "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
         "match_ms_per_step": [round(x, 3) for x in match_ms], "warmup_steps_run": warm_run,
-        "phases_ms": {k: p_last.get(k) for k in ("graph_ms", "windows_ms", "level2_ms", "match_ms", "fold_ms")},
+        "phases_ms": {k: p_last.get(k) for k in ("graph_ms", "windows_ms", "level2_ms", "match_ms", "ride_ms",
+                                                  "fold_ms")},
         "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                      "algorithmic_bytes": kb, "launch_ms": kms, "kernels": other},

@@ -288,6 +288,14 @@ typedef struct {
 } tm_tuning;
 int tm_get_tuning(tm_tuning* out);
 int tm_set_tuning(const tm_tuning* in);
+/* No counterpart in the paper: the matcher leaves the work of an exact query's riders (the
+ * estimates riding along with it) and smaller spans to a second kernel, as one record per group
+ * of instances, in a device buffer taken from the batch scratch.  `records` (1 .. 2^36) sets how
+ * many records the next batches make room for (default 2^23: 192 MB with 32-bit times, 256 MB
+ * with 64-bit times).  A batch that needs more runs a second time with room for all of them and
+ * raises the capacity to that, so the setting changes only memory and time, never a result.
+ * Returns TM_EINVAL outside that range. */
+int tm_set_ride_capacity(int64_t records);
 /* Time candidate tunings on `queries` over g (results discarded) and keep the
  * fastest; *best receives it.  Candidates: 128 or 256 threads, 4, 6, 8 or 12
  * blocks per SM, chunks of 256, 1024 or 4096 items, and (only when the batch
@@ -313,6 +321,9 @@ typedef struct {
     double sizing_ms;       /* last batch: first-edge count to the host, per-edge scratch,
                                window-of-block index (between windows_ms and level2_ms) */
     double scan_ms;         /* last batch: scan of the range lengths, chunk index */
+    double ride_ms;         /* last batch: the deferred pass of riders and smaller spans (k_ride),
+                               after the matcher; 0 when no exact query carried any */
+    int64_t ride_records;   /* last batch: records the matcher left to that pass */
 } tm_profile;
 int tm_profile_enable(int32_t on);
 /* Return device memory that freed graphs and batch scratch left in the library's

@@ -35,8 +35,9 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void store_profile_batch(double windows_ms, double level2_ms, double match_ms, double fold_ms,
                          double batch_ms, int64_t match_items, int64_t first_edges, double sizing_ms,
-                         double scan_ms) {
+                         double scan_ms, double ride_ms) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.ride_ms = ride_ms;
     g_prof.sizing_ms = sizing_ms;
     g_prof.scan_ms = scan_ms;
     g_prof.windows_ms = windows_ms;
@@ -46,6 +47,11 @@ void store_profile_batch(double windows_ms, double level2_ms, double match_ms, d
     g_prof.batch_ms = batch_ms;
     g_prof.match_items = match_items;
     g_prof.first_edges = first_edges;
+}
+
+void store_profile_ride_records(int64_t n) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.ride_records = n;
 }
 
 void store_profile_graph(double graph_ms) {

@@ -20,6 +20,7 @@
 //              query: Z_k = sum_j W_j / q_j per shift and the mean over shifts
 //              (Algorithm 1's return value).
 #include <algorithm>
+#include <atomic>
 #include <limits>
 #include <chrono>
 #include <cmath>
@@ -34,6 +35,13 @@ namespace tmo {
 Tuning& tuning() {
     static Tuning t;
     return t;
+}
+
+// Records the deferred-rider buffer of a batch holds: grows to the largest count a batch has
+// needed (tm_set_ride_capacity sets it)
+std::atomic<int64_t>& ride_capacity() {
+    static std::atomic<int64_t> cap{(int64_t)1 << 23};
+    return cap;
 }
 
 namespace {
@@ -78,6 +86,20 @@ struct FRec {
 };
 static_assert(sizeof(FRec<int32_t>) == 32 && sizeof(FRec<int64_t>) == 40, "first-edge record layout");
 
+// Instances of an exact query that its riders and smaller spans still have to weigh, deferred
+// by k_match to k_ride (so the matcher's hot loop carries none of their chains of loads): the
+// closing entries [x, x + n) of pair_t after time tc, or, for n < 0, -n instances whose last
+// edge is at time x.
+template <typename TT>
+struct RideRec {
+    int64_t x;
+    TT t1;       // the instances' first-edge time
+    TT tc;       // range records: the time after which the closing entries lie
+    int32_t q;   // the exact query
+    int32_t n;
+};
+static_assert(sizeof(RideRec<int32_t>) == 24 && sizeof(RideRec<int64_t>) == 32, "rider record layout");
+
 template <typename TT>
 struct MatchArgs {
     GraphDevT<TT> G;
@@ -99,6 +121,9 @@ struct MatchArgs {
     const int64_t* chunkf = nullptr;    // [nchunkf] first edge of work item i * chunk (null: searched)
     int64_t nchunkf = 0;
     bool ride = false;                  // estimates ride along with exact queries of the batch
+    RideRec<TT>* rrec = nullptr;        // [rcap] deferred rider / smaller-span work (see RideRec)
+    unsigned long long* rcount = nullptr;   // records appended (counts past rcap: the batch reruns)
+    int64_t rcap = 0;
 };
 
 // ----------------------------------------------------------------- helpers
@@ -1174,6 +1199,8 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
 #pragma unroll
             for (int i = 0; i < KMAX; i++) phi[i] = -1;
             bool deeper = false;
+            int64_t rx = 0;   // this item's deferred rider / smaller-span record (rn != 0)
+            int32_t rn = 0;
             if (valid) {
                 int64_t f = TM_CHK_IDX(fw, F, kChkQueue);
                 const FRec<TT> r = A.rec[f];
@@ -1195,7 +1222,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     int64_t cnt = (__ldg(S + j + 1) - __ldg(S + j)) - A.hs_hi[f];
                     if (Q.mode == TM_MODE_EXACT) {
                         // the query's own count came from the tables: the items are its riders'
-                        if (cnt > 0 && Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
+                        if (cnt > 0 && Q.nride) { rx = t3; rn = -(int32_t)cnt; }
                     } else {
                         acc_switch(acc, win, A.W.acc);
                         acc.s(A_CAND) += 1;
@@ -1233,8 +1260,7 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     if (cnt) {
                         acc.f[A_COUNT] += cnt;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
-                        if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
-                        if (Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
+                        if (Q.nsub | Q.nride) { rx = t3; rn = -(int32_t)cnt; }
                     }
                 } else {
                 // Two item kinds end in a count of one pair's entries in a time range: a
@@ -1303,16 +1329,30 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
                     if (cnt) {
                         acc.f[A_COUNT] += cnt;
                         if (Q.mode == TM_MODE_ESTIMATE) add_weight_n(acc, Q, t3 - t1, (unsigned long long)cnt);
-                        if (Q.nsub) add_sub_at(acc, Q, t1, t3, (unsigned long long)cnt);
-                        if (Q.nride) ride_at(PL, Q, A.W.kept, A.W.acc, t1, t3, (unsigned long long)cnt);
+                        if (Q.nsub | Q.nride) { rx = t3; rn = -(int32_t)cnt; }
                     }
                 } else if (kind == 2) {
                     // close the instance here: the last edge is counted by range length
                     acc.f[A_COUNT] += chi - clo;
                     acc.s(A_LAST) += 1;
-                    if (Q.nsub && chi > clo) add_sub_range(acc, Q, G.pair_t, clo, chi, t1);
-                    if (Q.nride && chi > clo) ride_range(PL, Q, A.W.kept, A.W.acc, G.pair_t, clo, chi, t1, tc);
+                    if ((Q.nsub | Q.nride) && chi > clo) { rx = clo; rn = (int32_t)(chi - clo); }
                 }
+                }
+            }
+            // the round's deferred records, appended with one atomic per warp
+            const unsigned rm = __ballot_sync(kFull, rn != 0);
+            if (rm) {
+                unsigned long long rb = 0;
+                if (lane == 0) rb = atomicAdd(A.rcount, (unsigned long long)__popc(rm));
+                rb = __shfl_sync(kFull, rb, 0) + __popc(rm & ((1u << lane) - 1u));
+                if (rn && (int64_t)rb < A.rcap) {
+                    RideRec<TT> rr;
+                    rr.x = rx;
+                    rr.t1 = (TT)t1;
+                    rr.tc = (TT)tc;
+                    rr.q = q;
+                    rr.n = rn;
+                    A.rrec[rb] = rr;
                 }
             }
             if constexpr (EXPAND) {
@@ -1339,6 +1379,153 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
             if (tab->cnt[i]) atomicAdd(p + A_COUNT, tab->cnt[i]);
             atomic_add_u128(p + A_WLO, tab->lo[i], tab->hi[i]);
         }
+    }
+}
+
+// Rider sums of one warp of k_ride records that all belong to exact query Q: every lane weighs
+// its own record per rider and shift, and when the lanes with instances share one window (the
+// usual case: neighbouring records come from the same first edges) their sums are added once,
+// by one lane, instead of 32 times to the same shared-memory slot.
+template <typename TT>
+__device__ __forceinline__ void ride_warp(const QPlan* __restrict__ PL, const QPlan& Q,
+                                          const int32_t* __restrict__ kept, unsigned long long* acc,
+                                          const TT* __restrict__ ta, bool valid, const RideRec<TT>& r) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t1 = (int64_t)r.t1, tc = (int64_t)r.tc;
+    const bool at = r.n < 0;
+    unsigned long long nread = 0;
+    for (int rr = 0; rr < Q.nride; rr++) {
+        const QPlan& R = PL[Q.ride_q[rr]];
+        const bool all_kept = R.q_mode == TM_Q_UNIFORM && R.p >= 1.0;   // no keep flag to read
+        for (int k = 0; k < R.b; k++) {
+            unsigned long long cnt = 0, wl = 0, wh = 0;
+            int64_t w = -1;
+            if (valid) {
+                int64_t thi;
+                ride_window(R, k, t1, w, thi);
+                if (at) {
+                    const int64_t t3 = r.x;   // -n instances closed at t3
+                    if (t3 - t1 <= R.delta && t3 <= thi && (all_kept || kept[w])) {
+                        cnt = (unsigned long long)(-(int64_t)r.n);
+                        ride_weight(R, t3 - t1, cnt, wl, wh);
+                    }
+                } else if (t1 + R.delta > tc && thi > tc && (all_kept || kept[w])) {
+                    for (int64_t x = r.x; x < r.x + r.n; x++) {
+                        const int64_t t3 = (int64_t)ta[x];
+                        if (t3 > thi) break;   // times increase
+                        unsigned long long l, h;
+                        ride_weight(R, t3 - t1, 1, l, h);
+                        const unsigned long long y = wl + l;
+                        wh += h + (y < wl ? 1ull : 0ull);
+                        wl = y;
+                        cnt++;
+                    }
+                    nread = max(nread, cnt);
+                }
+            }
+            const unsigned hm = __ballot_sync(kFull, cnt != 0);
+            if (!hm) continue;
+            const int first = __ffs(hm) - 1;
+            const int64_t w0 = __shfl_sync(kFull, w, first);
+            if (__all_sync(kFull, cnt == 0 || w == w0)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    cnt += __shfl_xor_sync(kFull, cnt, o);
+                    const unsigned long long l2 = __shfl_xor_sync(kFull, wl, o);
+                    const unsigned long long h2 = __shfl_xor_sync(kFull, wh, o);
+                    const unsigned long long y = wl + l2;
+                    wh = wh + h2 + (y < wl ? 1ull : 0ull);
+                    wl = y;
+                }
+                if (lane == first) ride_add(acc, w0, cnt, wl, wh);
+            } else if (cnt) {
+                ride_add(acc, w, cnt, wl, wh);
+            }
+        }
+    }
+    // entries read one by one: per record the most any rider shift read, summed over the warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nread += __shfl_xor_sync(kFull, nread, o);
+    if (lane == 0 && nread) ride_add(acc, (int64_t)(kInstKey | (unsigned long long)Q.win_base), nread, 0, 0);
+}
+
+// The deferred half of the exact queries that carry riders or smaller spans: one thread per
+// record of k_match (grid-stride, every lane busy), adding the smaller spans' counts to the
+// query's window and each rider's weighted instances to the rider's kept windows, exactly as
+// the matcher would have on the spot (integer sums: the order does not matter).
+template <typename TT>
+__global__ void __launch_bounds__(256) k_ride(MatchArgs<TT> A) {
+    const GraphDevT<TT>& G = A.G;
+    extern __shared__ __align__(16) unsigned char smem_plans[];
+    const QPlan* PL = stage_plans(A.plans, A.nq, smem_plans);
+    Acc acc;
+    acc_init(acc, smem_plans, A.nq);
+    acc_zero(acc);
+    RideTab* tab = ride_tab();
+    for (int i = threadIdx.x; i < kRideTab; i += blockDim.x) {
+        tab->key[i] = kTabFree;
+        tab->cnt[i] = tab->lo[i] = tab->hi[i] = 0;
+    }
+    __syncthreads();
+    const int64_t nrec = min((int64_t)*A.rcount, A.rcap);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps step together, so that the accumulator flushes see every lane
+    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t end = (nrec + 31) / 32 * 32;
+    for (int64_t i = start; i < end; i += stride) {
+        const bool valid = i < nrec;
+        RideRec<TT> r = {};
+        int64_t win = -1;
+        int32_t q = -1;
+        if (valid) {
+            r = A.rrec[i];
+            q = (int32_t)TM_CHK_IDX(r.q, A.nq, kChkWindow);
+            win = PL[q].win_base;
+        }
+        if (__any_sync(kFull, valid && acc.win != win)) {
+            acc_flush_warp(acc, A.W.acc);
+            if (valid) acc.win = win;
+        }
+        if (valid) {
+            const QPlan& Q = PL[q];
+            const int64_t t1 = (int64_t)r.t1;
+            if (r.n < 0) {
+                // (a two-node query's smaller spans were counted from the pair tables in k_level2;
+                // its records are for the riders only)
+                if (Q.nsub && !Q.ex23) add_sub_at(acc, Q, t1, r.x, (unsigned long long)(-(int64_t)r.n));
+            } else {
+                r.x = TM_CHK_IDX(r.x, G.m, kChkView);
+                TM_CHK(r.x + r.n <= G.m, kChkRange);
+#ifdef TM_CHECKED
+                if (r.x + r.n > G.m) r.n = 0;
+#endif
+                if (Q.nsub) add_sub_range(acc, Q, G.pair_t, r.x, r.x + r.n, t1);
+            }
+        }
+        // riders: warp by warp when the warp's records belong to one query (the valid lanes are
+        // a prefix of the warp, so lane 0 holds one), else lane by lane
+        const int32_t q0 = __shfl_sync(kFull, q, 0);
+        const bool uniform = __all_sync(kFull, !valid || q == q0);
+        if (uniform && q0 >= 0) {
+            if (PL[q0].nride) ride_warp(PL, PL[q0], A.W.kept, A.W.acc, G.pair_t, valid, r);
+        } else if (!uniform && valid && PL[q].nride) {
+            const QPlan& Q = PL[q];
+            if (r.n < 0) ride_at(PL, Q, A.W.kept, A.W.acc, (int64_t)r.t1, r.x, (unsigned long long)(-(int64_t)r.n));
+            else ride_range(PL, Q, A.W.kept, A.W.acc, G.pair_t, r.x, r.x + r.n, (int64_t)r.t1, (int64_t)r.tc);
+        }
+    }
+    acc_flush_warp(acc, A.W.acc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRideTab; i += blockDim.x) {
+        const unsigned long long key = tab->key[i];
+        if (key == kTabFree) continue;
+        if (key & kInstKey) {
+            atomicAdd(A.W.acc + (key & ~kInstKey) * A_N + A_INST, tab->cnt[i]);
+            continue;
+        }
+        unsigned long long* p = A.W.acc + (int64_t)key * A_N;
+        if (tab->cnt[i]) atomicAdd(p + A_COUNT, tab->cnt[i]);
+        atomic_add_u128(p + A_WLO, tab->lo[i], tab->hi[i]);
     }
 }
 
@@ -1748,6 +1935,7 @@ size_t per_first_scratch_bytes(int64_t F, bool hoist, size_t rec_bytes) {
 }
 constexpr size_t kBoundScratchBytes = (size_t)2 << 30;
 
+
 template <typename TT>
 int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, cudaStream_t st,
                 BatchOut* dbg) {
@@ -1825,6 +2013,13 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                           a256(8 * (size_t)hp[(size_t)i].b * (size_t)(hp[(size_t)i].J + 1));
         }
     }
+    // exact queries with riders or smaller spans leave that work to k_ride in records; the
+    // record buffer holds as many as the largest batch so far needed (a batch that needs more
+    // runs again with room for all of them)
+    bool any_share = false;
+    for (const QPlan& P : hp) any_share |= P.nsub > 0 || P.nride > 0;
+    const int64_t rcap = any_share ? ride_capacity().load() : 0;
+    const size_t rrec_bytes = any_share ? a256(sizeof(RideRec<TT>) * (size_t)rcap) : 0;
     // window origins of the riding estimates' shifts, read per instance on the device
     std::vector<int64_t> h_shifts;
     for (const QPlan& P : hp)
@@ -1839,7 +2034,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     size_t NWs = (size_t)std::max<int64_t>(NW, 1);
     size_t Ms = (size_t)std::max<int64_t>(g->m, 1);
     size_t sz = a256(sizeof(QPlan) * (size_t)nq) + a256(sizeof(tm_result) * (size_t)nq) + wtab_bytes +
-                9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 3 * 256 +
+                9 * a256(8 * NWs) + 3 * a256(4 * NWs) + a256(8 * NWs) + a256(8 * A_N * NWs) + 4 * 256 +
                 full_bytes + (any_full ? 3 * a256(4 * Ms) : 0) +
                 a256(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1)) +
                 a256(sizeof(ShiftSums) * (size_t)n_parts) +
@@ -1881,6 +2076,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     int64_t* dF = (int64_t*)take(8);
     int64_t* dW2 = (int64_t*)take(8);
     unsigned long long* dctr = (unsigned long long*)take(8);
+    unsigned long long* drcount = (unsigned long long*)take(8);
     ShiftSums* dsums = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)std::max<int64_t>(n_sums, 1));
     ShiftSums* dpart = (ShiftSums*)take(sizeof(ShiftSums) * (size_t)n_parts);
     unsigned long long* dsubc = (unsigned long long*)take(8 * kMaxSub * (size_t)nq);
@@ -1899,13 +2095,15 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     NvtxPhases nv;
     nv.next("tm_windows");
     auto wall0 = std::chrono::steady_clock::now();
-    int ev_w0 = pe.mark(st), ev_w1 = -1, ev_l0 = -1, ev_l1 = -1, ev_l2 = -1, ev_m1 = -1, ev_f1 = -1;
+    int ev_w0 = pe.mark(st), ev_w1 = -1, ev_l0 = -1, ev_l1 = -1, ev_l2 = -1, ev_m1 = -1, ev_r1 = -1, ev_f1 = -1;
     int64_t hW2 = 0;
+    unsigned long long h_rcount = 0;
     fail(cudaMemcpyAsync(dplans, hp.data(), sizeof(QPlan) * (size_t)nq, cudaMemcpyHostToDevice, st), "plans");
     if (!h_shifts.empty())
         fail(cudaMemcpyAsync(dshifts, h_shifts.data(), 8 * h_shifts.size(), cudaMemcpyHostToDevice, st), "shifts");
     fail(cudaMemsetAsync(W.acc, 0, 8 * A_N * NWs, st), "acc");
     fail(cudaMemsetAsync(dctr, 0, 8, st), "counter");
+    fail(cudaMemsetAsync(drcount, 0, 8, st), "record counter");
     for (int i = 0; i < nq && rc == TM_OK; i++) {
         const QPlan& P = hp[(size_t)i];
         if (P.wtab) {
@@ -1962,7 +2160,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     if (rc == TM_OK && Fa > 0) {
         size_t Fs = (size_t)Fa;
         size_t nbw = Fs / 32 + 1, ncf = Fs / 4 + 2;
-        rc = scratch_acquire(per_first_scratch_bytes(Fa, any_hoist, sizeof(FRec<TT>)), st, fb);
+        rc = scratch_acquire(per_first_scratch_bytes(Fa, any_hoist, sizeof(FRec<TT>)) + rrec_bytes, st, fb);
         if (rc == TM_OK) {
             char* q2 = (char*)fb.p;
             auto take2 = [&](size_t bytes) { char* r = q2; q2 += a256(bytes); return (void*)r; };
@@ -1973,6 +2171,7 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             int64_t* hs_hi = any_hoist ? (int64_t*)take2(8 * Fs) : nullptr;
             int32_t* bwin = (int32_t*)take2(4 * nbw);
             int64_t* cf = (int64_t*)take2(8 * ncf);
+            RideRec<TT>* rrec = any_share ? (RideRec<TT>*)take2(sizeof(RideRec<TT>) * (size_t)rcap) : nullptr;
             MatchArgs<TT> A;
             const int64_t* d_Fk = bounded ? dF : nullptr;
             A.G = G; A.plans = dplans; A.nq = nq; A.W = W; A.NW = NW; A.F = Fa; A.d_F = d_Fk;
@@ -1982,6 +2181,9 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             A.chunk = tu.chunk_items;
             A.blockwin = bwin; A.chunkf = cf; A.nchunkf = (int64_t)ncf;
             A.ride = !h_shifts.empty();
+            A.rrec = rrec;
+            A.rcount = drcount;
+            A.rcap = rcap;
             int64_t gl2 = std::min<int64_t>((Fa + 255) / 256, (int64_t)nsm * 8);
             k_blockwin<<<(unsigned)std::min<int64_t>(((int64_t)nbw + 255) / 256, (int64_t)nsm * 8), 256, 0, st>>>(
                 W.fbase, NW, Fa, d_Fk, bwin);
@@ -2006,6 +2208,13 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
                                  std::any_of(hp.begin(), hp.end(), [](const QPlan& P) { return plan_expands(P); }));
                 fail(cudaGetLastError(), "k_match");
                 ev_m1 = pe.mark(st);
+                if (any_share && rc == TM_OK) {
+                    nv.next("tm_ride");
+                    k_ride<TT><<<(unsigned)(nsm * 8), 256, match_smem_bytes(A.nq, 256, true), st>>>(A);
+                    count_launch();
+                    fail(cudaGetLastError(), "k_ride");
+                    ev_r1 = pe.mark(st);
+                }
                 if (pe.on) fail(cudaMemcpyAsync(&hW2, dW2, 8, cudaMemcpyDeviceToHost, st), "W2");
                 if (pe.on && bounded) fail(cudaMemcpyAsync(&F, dF, 8, cudaMemcpyDeviceToHost, st), "F");
             }
@@ -2020,7 +2229,9 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
         ev_f1 = pe.mark(st);
         nv.next(nullptr);
         if (ev_m1 < 0) ev_m1 = ev_f0;
+        if (ev_r1 < 0) ev_r1 = ev_m1;
     }
+    if (rc == TM_OK && any_share) fail(cudaMemcpyAsync(&h_rcount, drcount, 8, cudaMemcpyDeviceToHost, st), "records");
     if (rc == TM_OK) fail(cudaMemcpyAsync(res, dres, sizeof(tm_result) * (size_t)nq, cudaMemcpyDeviceToHost, st), "results");
     if (rc == TM_OK && dbg && dbg->sub_count)
         fail(cudaMemcpyAsync(dbg->sub_count, dsubc, 8 * kMaxSub * (size_t)nq, cudaMemcpyDeviceToHost, st),
@@ -2060,12 +2271,21 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
     if (pe.on && rc == TM_OK) {
         double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
         store_profile_batch(pe.ms(ev_w0, ev_w1), pe.ms(ev_l0, ev_l2), ev_l1 >= 0 ? pe.ms(ev_l1, ev_m1) : 0.0,
-                            pe.ms(ev_m1 >= 0 && ev_l1 >= 0 ? ev_m1 : ev_f1, ev_f1), wall, hW2, F,
-                            ev_l0 >= 0 ? pe.ms(ev_w1, ev_l0) : 0.0, ev_l1 >= 0 ? pe.ms(ev_l2, ev_l1) : 0.0);
+                            pe.ms(ev_m1 >= 0 && ev_l1 >= 0 ? ev_r1 : ev_f1, ev_f1), wall, hW2, F,
+                            ev_l0 >= 0 ? pe.ms(ev_w1, ev_l0) : 0.0, ev_l1 >= 0 ? pe.ms(ev_l2, ev_l1) : 0.0,
+                            ev_l1 >= 0 ? pe.ms(ev_m1, ev_r1) : 0.0);
     }
+    if (pe.on && rc == TM_OK) store_profile_ride_records((int64_t)h_rcount);
     scratch_release(fb, st);
     cudaFreeAsync(sb, st);
     if (rc != TM_OK) return rc;
+    if ((int64_t)h_rcount > rcap) {
+        // more deferred records than the buffer held: run again with room for all of them
+        int64_t want = (int64_t)h_rcount + (int64_t)(h_rcount >> 3) + 1024;
+        int64_t cur = ride_capacity().load();
+        while (cur < want && !ride_capacity().compare_exchange_weak(cur, want)) {}
+        return run_batch_t<TT>(g, qs, nq, res, st, dbg);
+    }
     if (dbg && dq_n > 0) {
         const QPlan& P = hp[(size_t)dbg->query];
         int64_t n_out = 0;
@@ -2780,5 +3000,14 @@ int tm_batch_results(tm_batch* b, void* stream, tm_result* results) {
 }
 
 void tm_batch_free(tm_batch* b) { tmo::batch_release(b); }
+
+int tm_set_ride_capacity(int64_t records) {
+    if (records < 1 || records > ((int64_t)1 << 36)) {
+        tmo::set_error("ride capacity outside [1, 2^36] records");
+        return TM_EINVAL;
+    }
+    tmo::ride_capacity().store(records);
+    return TM_OK;
+}
 
 }  // extern "C"

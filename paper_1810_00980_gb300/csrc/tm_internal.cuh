@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/tm.h"
@@ -281,6 +282,7 @@ struct Tuning {
     int enum_threshold = 48;
 };
 Tuning& tuning();
+std::atomic<int64_t>& ride_capacity();
 
 // one query's part of a segment of a streamed graph
 struct SegSpec {
@@ -375,8 +377,9 @@ void scratch_release(ScratchLease& L, cudaStream_t st);
 bool profiling();
 void store_profile_batch(double windows_ms, double level2_ms, double match_ms, double fold_ms,
                          double batch_ms, int64_t match_items, int64_t first_edges, double sizing_ms,
-                         double scan_ms);
+                         double scan_ms, double ride_ms = 0.0);
 void store_profile_graph(double graph_ms);
+void store_profile_ride_records(int64_t n);
 void count_launch(int n = 1);
 
 // NVTX ranges naming the host-side phases of a call (graph build, window partition, second-edge
@@ -395,20 +398,21 @@ struct NvtxPhases {
 
 // CUDA events on a stream, created only while profiling is on
 struct PhaseEvents {
-    cudaEvent_t ev[8];
+    static constexpr int kMax = 12;
+    cudaEvent_t ev[kMax];
     int n = 0;
     bool on = false;
     explicit PhaseEvents(bool enable) : on(enable) {
         if (on)
-            for (int i = 0; i < 8; i++)
+            for (int i = 0; i < kMax; i++)
                 if (cudaEventCreate(&ev[i]) != cudaSuccess) on = false;
     }
     ~PhaseEvents() {
         if (on)
-            for (int i = 0; i < 8; i++) cudaEventDestroy(ev[i]);
+            for (int i = 0; i < kMax; i++) cudaEventDestroy(ev[i]);
     }
     int mark(cudaStream_t st) {
-        if (!on || n >= 8) return -1;
+        if (!on || n >= kMax) return -1;
         cudaEventRecord(ev[n], st);
         return n++;
     }

@@ -66,7 +66,8 @@ class ServeCfg(ctypes.Structure):
 class ProfileC(ctypes.Structure):
     _fields_ = [("graph_ms", _c_dbl), ("windows_ms", _c_dbl), ("level2_ms", _c_dbl), ("match_ms", _c_dbl),
                 ("fold_ms", _c_dbl), ("batch_ms", _c_dbl), ("match_items", _c_i64), ("first_edges", _c_i64),
-                ("launches", _c_i64), ("sizing_ms", _c_dbl), ("scan_ms", _c_dbl)]
+                ("launches", _c_i64), ("sizing_ms", _c_dbl), ("scan_ms", _c_dbl),
+                ("ride_ms", _c_dbl), ("ride_records", _c_i64)]
 
 
 class TmError(RuntimeError):
@@ -104,6 +105,7 @@ _SIGS = {
     "tm_batch_free": (None, [_vp]),
     "tm_get_tuning": (ctypes.c_int, [_vp]),
     "tm_set_tuning": (ctypes.c_int, [_vp]),
+    "tm_set_ride_capacity": (ctypes.c_int, [_c_i64]),
     "tm_autotune": (ctypes.c_int, [_vp, _vp, _c_i32, _vp]),
     "tm_profile_enable": (ctypes.c_int, [_c_i32]),
     "tm_profile_last": (ctypes.c_int, [_vp]),
@@ -430,6 +432,10 @@ def get_tuning() -> dict:
 def set_tuning(**kw):
     t = TuningC(**{k: int(v) for k, v in kw.items()})
     _check(lib().tm_set_tuning(ctypes.byref(t)), "tm_set_tuning")
+
+
+def set_ride_capacity(records: int):
+    _check(lib().tm_set_ride_capacity(int(records)), "tm_set_ride_capacity")
 
 
 def autotune(g: Graph, queries) -> dict:

@@ -50,10 +50,10 @@ def test_nm_shows_exports(built):
 def test_struct_layouts_match_c(built, tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tm.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                     'sizeof(tm_graph_info), sizeof(tm_window_rec), sizeof(tm_query), sizeof(tm_result),'
                     'sizeof(tm_tuning), sizeof(tm_serve_cfg), offsetof(tm_result, var_hat),'
-                    'offsetof(tm_profile, launches),'
+                    'offsetof(tm_profile, launches), sizeof(tm_profile),'
                     'offsetof(tm_query, q_mode), sizeof(tm_stream_stats),'
                     'offsetof(tm_stream_stats, copy_wait_ms));return 0;}\n')
     exe = tmp_path / "sz"
@@ -63,7 +63,8 @@ def test_struct_layouts_match_c(built, tmp_path):
     tm = built
     assert vals == [ctypes.sizeof(tm.GraphInfo), ctypes.sizeof(tm.WindowRec), ctypes.sizeof(tm.QueryC),
                     ctypes.sizeof(tm.ResultC), ctypes.sizeof(tm.TuningC), ctypes.sizeof(tm.ServeCfg),
-                    tm.ResultC.var_hat.offset, tm.ProfileC.launches.offset, tm.QueryC.q_mode.offset,
+                    tm.ResultC.var_hat.offset, tm.ProfileC.launches.offset, ctypes.sizeof(tm.ProfileC),
+                    tm.QueryC.q_mode.offset,
                     ctypes.sizeof(tm.StreamStatsC), tm.StreamStatsC.copy_wait_ms.offset]
 
 

@@ -744,6 +744,42 @@ def test_estimates_ride_along_exact_queries(tm, orc):
         assert alone["var_hat"] == r["var_hat"] and alone["shift_var"] == r["shift_var"]
 
 
+def test_deferred_rider_records_overflow_reruns(tm, orc):
+    """The matcher leaves riders and smaller spans to a second pass through a record buffer; a
+    batch that needs more records than the buffer holds runs again with room for all of them.
+    With the capacity set to 16 records the results equal those at the default capacity bit for
+    bit, and the oracle's."""
+    src, dst, t = synth.chung_lu_hawkes(1500, 80_000, 2.1, seed=41, horizon=3_000_000)
+    g = _graph(tm, src, dst, t)
+    ms, md = synth.MOTIFS["cycle3"]
+    mo = tm.Motif(ms, md)
+    ms2, md2 = synth.MOTIFS["pingpong"]
+    mo2 = tm.Motif(ms2, md2)
+    qs = [tm.exact_query(mo, 86400), tm.exact_query(mo, 3600),
+          tm.estimate_query(mo, 86400, 30, 1.0, 3), tm.estimate_query(mo, 3600, 10, 0.5, 4, b=2),
+          tm.exact_query(mo2, 86400), tm.estimate_query(mo2, 3600, 10, 0.5, 5)]
+    ref = tm.run_batch(g, qs)
+    tm.profile_enable(True)
+    try:
+        tm.set_ride_capacity(16)
+        res = tm.run_batch(g, qs)
+        records = tm.profile_last()["ride_records"]
+    finally:
+        tm.profile_enable(False)
+        tm.set_ride_capacity(1 << 23)
+    assert records > 16, records
+    for r, w in zip(res, ref):
+        assert r["status"] == 0
+        assert r["count"] == w["count"] and r["estimate"] == w["estimate"]
+        assert r["var_hat"] == w["var_hat"] and r["windows_kept"] == w["windows_kept"]
+    assert res[0]["count"] == orc.count_exact(src, dst, t, ms, md, 86400, threads=8)
+    assert res[1]["count"] == orc.count_exact(src, dst, t, ms, md, 3600, threads=8)
+    assert _close(res[3]["estimate"], orc.estimate(src, dst, t, ms, md, 3600, 10, 0.5, 4, b=2, threads=8))
+    assert _close(res[5]["estimate"], orc.estimate(src, dst, t, ms2, md2, 3600, 10, 0.5, 5, threads=8))
+    with pytest.raises(tm.TmError):
+        tm.set_ride_capacity(0)
+
+
 def test_sharing_limits_and_mixes(tm, orc):
     """Batches that stretch the sharing rules: more spans than one leader carries, more
     estimates than riders allowed, equal spans, a rejected query, automatic p and q_j rules
