@@ -120,7 +120,6 @@ struct MatchArgs {
     const int32_t* blockwin = nullptr;  // [ceil(F/32)] window of first edge 32 b (null: searched)
     const int64_t* chunkf = nullptr;    // [nchunkf] first edge of work item i * chunk (null: searched)
     int64_t nchunkf = 0;
-    bool ride = false;                  // estimates ride along with exact queries of the batch
     RideRec<TT>* rrec = nullptr;        // [rcap] deferred rider / smaller-span work (see RideRec)
     unsigned long long* rcount = nullptr;   // records appended (counts past rcap: the batch reruns)
     int64_t rcap = 0;
@@ -440,9 +439,12 @@ __device__ __forceinline__ void ride_window(const QPlan& R, int k, int64_t t1, i
 
 // Rider sums go through a per-block table in shared memory keyed by window (when c delta is
 // long, a handful of windows take most instances, and the same few global words would
-// otherwise be hit by every SM), flushed to the global sums when the block ends.  The table
-// sits at the end of k_match's dynamic shared memory (batches with riders only).
-constexpr int kRideTab = 128;
+// otherwise be hit by every SM; when it is short, a block's records still reach thousands of
+// windows), flushed to the global sums when the block ends.  A window takes a free slot among
+// kRideProbe from its hash; one that finds them all taken adds to the global sums.  The table
+// sits at the end of k_ride's dynamic shared memory.
+constexpr int kRideTab = 512;
+constexpr int kRideProbe = 4;
 constexpr unsigned long long kTabFree = ~0ull;
 constexpr unsigned long long kInstKey = 1ull << 62;   // key flag: an exact query's entries-read counter
 struct RideTab {
@@ -465,18 +467,22 @@ __device__ __forceinline__ void ride_add(unsigned long long* acc, int64_t w, uns
                                          unsigned long long lo, unsigned long long hi) {
     if (!cnt) return;
     RideTab* tab = ride_tab();
-    const int sl = (int)(w & (kRideTab - 1));
-    unsigned long long key = *(volatile unsigned long long*)&tab->key[sl];
-    if (key == kTabFree) {
-        unsigned long long old = atomicCAS(&tab->key[sl], kTabFree, (unsigned long long)w);
-        key = old == kTabFree ? (unsigned long long)w : old;
-    }
-    if (key == (unsigned long long)w) {
-        atomicAdd(&tab->cnt[sl], cnt);
-        unsigned long long old = atomicAdd(&tab->lo[sl], lo);
-        if (old + lo < old) hi += 1;
-        if (hi) atomicAdd(&tab->hi[sl], hi);
-        return;
+    const unsigned long long h = sm64_mix((unsigned long long)w);
+#pragma unroll
+    for (int pr = 0; pr < kRideProbe; pr++) {
+        const int sl = (int)((h + (unsigned long long)pr) & (kRideTab - 1));
+        unsigned long long key = *(volatile unsigned long long*)&tab->key[sl];
+        if (key == kTabFree) {
+            unsigned long long old = atomicCAS(&tab->key[sl], kTabFree, (unsigned long long)w);
+            key = old == kTabFree ? (unsigned long long)w : old;
+        }
+        if (key == (unsigned long long)w) {
+            atomicAdd(&tab->cnt[sl], cnt);
+            unsigned long long old = atomicAdd(&tab->lo[sl], lo);
+            if (old + lo < old) hi += 1;
+            if (hi) atomicAdd(&tab->hi[sl], hi);
+            return;
+        }
     }
     if ((unsigned long long)w & kInstKey) {
         atomicAdd(acc + ((unsigned long long)w & ~kInstKey) * A_N + A_INST, cnt);
@@ -1147,14 +1153,6 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
     Acc acc;
     acc_init(acc, smem_plans, A.nq);
     acc_zero(acc);
-    if (A.ride) {
-        RideTab* tab = ride_tab();
-        for (int i = threadIdx.x; i < kRideTab; i += blockDim.x) {
-            tab->key[i] = kTabFree;
-            tab->cnt[i] = tab->lo[i] = tab->hi[i] = 0;
-        }
-        __syncthreads();
-    }
     for (;;) {
         unsigned long long c0u = 0;
         if (lane == 0) c0u = atomicAdd(A.counter, (unsigned long long)A.chunk);
@@ -1365,21 +1363,6 @@ __global__ void __launch_bounds__(256, OCC) k_match(MatchArgs<TT> A) {
         acc_flush_warp(acc, A.W.acc);
     }
     acc_flush_warp(acc, A.W.acc);
-    if (A.ride) {   // every warp of the block is done: the rider sums go to the global windows
-        RideTab* tab = ride_tab();
-        __syncthreads();
-        for (int i = threadIdx.x; i < kRideTab; i += blockDim.x) {
-            const unsigned long long key = tab->key[i];
-            if (key == kTabFree) continue;
-            if (key & kInstKey) {
-                atomicAdd(A.W.acc + (key & ~kInstKey) * A_N + A_INST, tab->cnt[i]);
-                continue;
-            }
-            unsigned long long* p = A.W.acc + (int64_t)key * A_N;
-            if (tab->cnt[i]) atomicAdd(p + A_COUNT, tab->cnt[i]);
-            atomic_add_u128(p + A_WLO, tab->lo[i], tab->hi[i]);
-        }
-    }
 }
 
 // Rider sums of one warp of k_ride records that all belong to exact query Q: every lane weighs
@@ -1703,7 +1686,7 @@ void launch_match(const MatchArgs<TT>& A, int lmax, int kmax, const Tuning& tu, 
                   bool expand) {
     const int bps = tu.blocks_per_sm, bt = tu.block_threads;
     const unsigned gm = (unsigned)(nsm * bps);
-    const size_t sm = match_smem_bytes(A.nq, bt, A.ride);
+    const size_t sm = match_smem_bytes(A.nq, bt);
     if (lmax <= 3 && kmax <= 4 && !expand) {
         if (bps >= 6) k_match<TT, 3, 4, 6, false><<<gm, bt, sm, st>>>(A);
         else k_match<TT, 3, 4, 4, false><<<gm, bt, sm, st>>>(A);
@@ -2180,7 +2163,6 @@ int run_batch_t(const tm_graph* g, const tm_query* qs, int nq, tm_result* res, c
             A.enum_threshold = tu.enum_threshold;
             A.chunk = tu.chunk_items;
             A.blockwin = bwin; A.chunkf = cf; A.nchunkf = (int64_t)ncf;
-            A.ride = !h_shifts.empty();
             A.rrec = rrec;
             A.rcount = drcount;
             A.rcap = rcap;
