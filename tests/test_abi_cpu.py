@@ -115,3 +115,13 @@ def test_product_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower() or f == "synth.py", f
+
+
+def test_ride_capacity_is_checked_on_the_host(built):
+    """tm_set_ride_capacity takes 1 .. 2^36 records and rejects the rest (no device call)."""
+    tm = built
+    for bad in (0, -5, (1 << 36) + 1):
+        with pytest.raises(tm.TmError) as e:
+            tm.set_ride_capacity(bad)
+        assert e.value.status == tm.TM_EINVAL
+    tm.set_ride_capacity(1 << 23)   # the default
